@@ -1,0 +1,179 @@
+/*
+ * swe.h -- C ABI of the GB300 shallow-water MacCormack library.
+ *
+ * The library advances the 2D shallow-water equations with the explicit
+ * predictor-corrector MacCormack scheme of Seitz et al., "A GPU
+ * Implementation for Two-Dimensional Shallow Water Modeling" (2013): the
+ * unknowns are the free-surface elevation eta and the two depth-averaged
+ * velocities u, v of every cell of a structured grid (Sec. 1); one time step
+ * is the chain of 16 dependent sub-steps of Sec. 1, each independent per
+ * cell; the step size is variable (Sec. 3.1); drying, which the paper's code
+ * lacked (Sec. 6.2), is handled.  The sub-steps and every reading of what the
+ * paper leaves to Ransom's thesis are:
+ *   S1  h = eta - z, wet iff h > h_dry
+ *   S2  dt = min(cfl / max_wet[(|u|+sqrt(g h))/dx + (|v|+sqrt(g h))/dy], dt_max)
+ *       (dt_max when nothing is wet), reduced on the GPU in FP64
+ *   S3  ghost ring from the boundary conditions (below)
+ *   S4  fluxes h u, h v; face flux = flux of the downwind cell of the
+ *       predictor's one-sided difference; boundary faces: wall 0, inflow
+ *       q_in, outflow the adjacent cell's flux
+ *   S5  eta* = eta - dt (dFx/dx + dFy/dy)
+ *   S6  C = g n^2 |U| / h^(4/3) on wet cells, else 0
+ *   S7  u* = (u - dt (u u_x + v u_y + g eta_x)) / (1 + dt C), v* alike;
+ *       a dry neighbour whose bed is above the cell's surface is seen at the
+ *       cell's own elevation (a wall)
+ *   S8  h* < 0: eta* = z (tallied as clamp volume); h* <= h_dry: u* = v* = 0
+ *   S9-S13  the same on the predicted state with the opposite one-sided
+ *       differences, always updating from the level-n eta, u, v
+ *   S14 average of the predicted and corrected states
+ *   S15 artificial dissipation kappa * (eps (phi_{i+1}-phi_i) - eps (phi_i-phi_{i-1}))
+ *       per axis on eta, u, v of level n, eps = max of the two cells'
+ *       |h_{i-1}+h_{i+1}-2h_i| / (|h_{i-1}|+|h_{i+1}|+2|h_i|+1e-12), on
+ *       interior faces between two wet cells only
+ *   S16 the S8 fix on the new level, tallies.
+ * The predictor direction alternates every step (forward/forward, then
+ * backward/backward) unless dir_cycle says otherwise.
+ *
+ * Boundary conditions, per side W (x = 0), E, S (y = 0), N: WALL reflects the
+ * normal velocity (free slip); INFLOW prescribes the discharge per unit width
+ * q_in entering the domain; OUTFLOW is transmissive (zero gradient).
+ *
+ * Arrays.  Host arrays are ny*nx doubles, row-major, x fastest (cell (i,j)
+ * at j*nx+i), owned by the caller and copied.  Device-array calls take
+ * dense ny*nx arrays of the context's real type (double for SWE_FP64, float
+ * for SWE_FP32) on the context's device, ordered on the context's stream, and
+ * never keep the pointer.  The context owns every device buffer it uses.
+ *
+ * Errors.  Every call returns a swe_status; nothing throws or exits across
+ * the ABI.  swe_last_error gives a text for the last failure of a context.
+ * Calls on one context are not thread-safe; distinct contexts are
+ * independent.  A CUDA error poisons the context (SWE_ERR_STATE after it).
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SWE_OK = 0,
+    SWE_ERR_ARG = 1,        /* invalid argument, size or pointer */
+    SWE_ERR_CUDA = 2,       /* a CUDA call failed; text in swe_last_error */
+    SWE_ERR_NONFINITE = 3,  /* the state holds NaN or Inf after the call */
+    SWE_ERR_NEGDEPTH = 4,   /* input depth below -1e-12 m */
+    SWE_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SWE_ERR_STATE = 6,      /* call out of order, or context poisoned */
+    SWE_ERR_UNSUPPORTED = 7 /* configuration the called entry point does not handle */
+} swe_status;
+
+typedef enum { SWE_BC_WALL = 0, SWE_BC_INFLOW = 1, SWE_BC_OUTFLOW = 2 } swe_bc;
+typedef enum { SWE_SIDE_W = 0, SWE_SIDE_E = 1, SWE_SIDE_S = 2, SWE_SIDE_N = 3 } swe_side;
+typedef enum { SWE_FP64 = 0, SWE_FP32 = 1 } swe_precision;
+typedef enum {
+    SWE_KERNEL_FUSED = 0,   /* one sweep per step (default) */
+    SWE_KERNEL_PLAIN = 1    /* one thread per cell, predictor and corrector as two kernels */
+} swe_kernel;
+
+/* Step-info flag bits */
+#define SWE_FLAG_NONFINITE 1u
+#define SWE_FLAG_TIMEOUT 2u
+#define SWE_FLAG_CLAMPED 4u
+
+typedef struct {
+    int32_t nx, ny;         /* cells in x and y, >= 1 */
+    double dx, dy;          /* cell sizes, m, > 0 */
+    double g;               /* gravity, m/s^2 (9.81) */
+    double cfl;             /* Courant number of S2 (0.5) */
+    double h_dry;           /* wet/dry threshold, m (1e-3) */
+    double dt_max;          /* time-step cap, s (10) */
+    double kappa;           /* S15 coefficient, 0 = off, at most 0.25 */
+    double manning_n;       /* uniform Manning n, used without a per-cell field */
+    int32_t bc[4];          /* swe_bc per side, order W, E, S, N */
+    double q_in[4];         /* inflow discharge per unit width into the domain, m^2/s */
+    int32_t precision;      /* swe_precision */
+    int32_t dir_cycle;      /* bit 0: alternate directions per step; bit 1: x starts
+                               backward; bit 2: y starts backward (default 1) */
+    int32_t device;         /* CUDA device ordinal */
+    int32_t kernel;         /* swe_kernel */
+    void* stream;           /* cudaStream_t to order all work on; NULL: context-owned */
+    int32_t seg_rows;       /* fused kernel: rows per work item, 0 = automatic */
+    int32_t cta_warps;      /* fused kernel: warps per CTA, 0 = automatic */
+    int32_t use_graph;      /* capture multi-step calls in CUDA graphs (default 1) */
+    int32_t dry_skip;       /* skip all-dry work items (default 1) */
+    int32_t reserved[4];
+} swe_params;
+
+typedef struct {
+    double t;               /* simulated time, s */
+    double dt_last;         /* last step size, s */
+    double dt_min;          /* smallest step size of the call */
+    double dt_max_seen;     /* largest step size of the call */
+    double volume;          /* sum of h dx dy, m^3, summed in FP64 */
+    double clamp_volume;    /* water added by the negative-depth fix since creation, m^3 */
+    double bflux[4];        /* water entered through each side since creation, m^3 */
+    int64_t step;           /* global step index */
+    int64_t n_wet;          /* wet cells of the current state */
+    int32_t flags;          /* SWE_FLAG_* seen during the call */
+    int32_t pad;
+} swe_step_info;
+
+typedef struct swe_ctx swe_ctx;
+
+/* Fills p with the defaults named above (walls, FP64, fused kernel, alternating
+ * directions, device 0, own stream); nx, ny, dx, dy still need setting. */
+void swe_params_default(swe_params* p);
+
+/* Validates p, allocates the context and its device buffers (state ping-pong,
+ * bed, friction field, reduction scratch).  *out receives the context, or NULL
+ * on failure.  Bed and state start at zero until set. */
+swe_status swe_create(const swe_params* p, swe_ctx** out);
+
+/* Bed elevation z (m) and, optionally, a per-cell Manning n field (NULL: the
+ * uniform manning_n).  Host arrays, ny*nx. */
+swe_status swe_set_bed(swe_ctx* ctx, const double* z, const double* n_field);
+
+/* Initial state (host arrays).  A depth below -1e-12 m is SWE_ERR_NEGDEPTH;
+ * a smaller negative depth is clamped (eta = z); dry cells get zero velocity.
+ * Computes the first step's CFL reduction.  Keeps the step index and time. */
+swe_status swe_set_state(swe_ctx* ctx, const double* eta, const double* u, const double* v);
+
+/* Sets the step index (direction parity) and the simulated time. */
+swe_status swe_set_clock(swe_ctx* ctx, int64_t step, double t);
+
+/* Advances nsteps steps.  dt_fixed (nullable, host, nsteps values) replaces
+ * S2 by the given step sizes; dt_out (nullable, host, nsteps values) receives
+ * the step sizes used; info (nullable) receives the diagnostics at the end of
+ * the call (reading it synchronises the stream).  SWE_ERR_NONFINITE when the
+ * state holds NaN/Inf at the end. */
+swe_status swe_step(swe_ctx* ctx, int32_t nsteps, const double* dt_fixed, double* dt_out,
+                    swe_step_info* info);
+
+/* Current state to host arrays (synchronises the stream). */
+swe_status swe_get_state(swe_ctx* ctx, double* eta, double* u, double* v);
+
+/* Diagnostics of the current state (synchronises the stream). */
+swe_status swe_get_info(swe_ctx* ctx, swe_step_info* info);
+
+/* Device-array variants of set_state / get_state / set_bed (context real
+ * type, dense ny*nx, asynchronous on the context stream). */
+swe_status swe_set_state_device(swe_ctx* ctx, const void* eta, const void* u, const void* v);
+swe_status swe_get_state_device(swe_ctx* ctx, void* eta, void* u, void* v);
+swe_status swe_set_bed_device(swe_ctx* ctx, const void* z, const void* n_field);
+
+/* The context's CUDA stream (cudaStream_t). */
+void* swe_stream(const swe_ctx* ctx);
+
+/* Frees the context and every buffer it owns.  NULL is ignored. */
+void swe_destroy(swe_ctx* ctx);
+
+/* Text of the last failure on ctx (static text when ctx is NULL). */
+const char* swe_last_error(const swe_ctx* ctx);
+const char* swe_status_string(swe_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_H */

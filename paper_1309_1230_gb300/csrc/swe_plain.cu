@@ -1,0 +1,458 @@
+// swe_plain.cu -- the plain GPU step: one thread per cell, the predictor
+// (S1-S8) and the corrector with averaging, dissipation and fix (S9-S16) as
+// two kernels per step, all data in global memory.  This mirrors the paper's
+// non-shared-memory design (Sec. 3.1: kernel boundaries give the intra-step
+// synchronisation, one thread per cell), except that the time-step
+// reduction stays on the GPU.  It is the FP64/FP32 reference step that the
+// fused sweep is compared with, and the utility kernels of the context.
+#include <cfloat>
+
+#include "swe_internal.cuh"
+
+namespace swe {
+
+template <class T>
+__device__ __forceinline__ Cell<T> ld(const T* e, const T* u, const T* v, const T* z, size_t k) {
+    Cell<T> c;
+    c.e = e[k]; c.u = u[k]; c.v = v[k]; c.z = z[k];
+    return c;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T x) {
+    for (int o = 16; o > 0; o >>= 1) {
+        T y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+// Step size of step s of a call: replayed or from the level's CFL reduction.
+__global__ void k_plain_dt(DevCtl* ctl, int slot, int slot_next, const double* dt_fixed, int s,
+                           double* dt_hist, double cfl, double dt_max) {
+    double dt;
+    if (dt_fixed) dt = dt_fixed[s];
+    else dt = dt_from_speed(__longlong_as_double((long long)ctl->smax[slot]), cfl, dt_max);
+    ctl->dt_cur = dt;
+    ctl->dt_last = dt;
+    ctl->t += dt;
+    ctl->dt_min = fmin(ctl->dt_min, dt);
+    ctl->dt_maxs = fmax(ctl->dt_maxs, dt);
+    dt_hist[s] = dt;
+    ctl->smax[slot_next] = 0ull;
+}
+
+template <class T, int SX, int SY>
+__global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const DevCtl* __restrict__ ctl, double dx,
+                                                    double dy, double g, const T* __restrict__ e,
+                                                    const T* __restrict__ u, const T* __restrict__ v,
+                                                    const T* __restrict__ z, const T* __restrict__ n2,
+                                                    T* __restrict__ es, T* __restrict__ us,
+                                                    T* __restrict__ vs, DevCtl* ctl_w, double area) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const StepK<T> S = make_stepk<T>(ctl->dt_cur, dx, dy, g);
+    T added = T(0);
+    if (i < G.nx && j < G.ny) {
+        const size_t k = (size_t)j * G.pitch + i;
+        Cell<T> c = ld(e, u, v, z, k);
+        Cell<T> xn = (i + SX >= 0 && i + SX < G.nx) ? ld(e, u, v, z, (size_t)((ptrdiff_t)k + SX))
+                                                   : ghost(c, SX > 0 ? SIDE_E : SIDE_W, G);
+        Cell<T> yn = (j + SY >= 0 && j + SY < G.ny) ? ld(e, u, v, z, (size_t)((ptrdiff_t)k + (ptrdiff_t)SY * G.pitch))
+                                                   : ghost(c, SY > 0 ? SIDE_N : SIDE_S, G);
+        T gn2 = n2 ? n2[k] : G.gn2;
+        T fe, fw, fn, fs;
+        faces<SX>((c.e - c.z) * c.u, (xn.e - xn.z) * xn.u, i == 0, i == G.nx - 1, SIDE_W, SIDE_E, G, fe, fw);
+        faces<SY>((c.e - c.z) * c.v, (yn.e - yn.z) * yn.v, j == 0, j == G.ny - 1, SIDE_S, SIDE_N, G, fn, fs);
+        T eo, uo, vo;
+        stage<SX, SY>(c, xn, yn, fe, fw, fn, fs, c.e, c.u, c.v, gn2, S, G.h_dry, eo, uo, vo);
+        added = wetdry_fix(eo, uo, vo, c.z, G.h_dry);
+        es[k] = eo; us[k] = uo; vs[k] = vo;
+    }
+    // predictor clamps count half (the average keeps half of the predicted level)
+    if (__any_sync(0xffffffffu, added != T(0))) {
+        double s = warp_sum((double)added);
+        if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&ctl_w->clamp, 0.5 * s * area);
+    }
+}
+
+template <class T, int SX, int SY>
+__global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, double dx, double dy, double g,
+                                                    const T* __restrict__ e, const T* __restrict__ u,
+                                                    const T* __restrict__ v, const T* __restrict__ z,
+                                                    const T* __restrict__ n2, const T* __restrict__ es,
+                                                    const T* __restrict__ us, const T* __restrict__ vs,
+                                                    T* __restrict__ e1, T* __restrict__ u1,
+                                                    T* __restrict__ v1, int slot_next, double area) {
+    constexpr int CX = -SX, CY = -SY;  // corrector directions
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const double dtd = ctl->dt_cur;
+    const StepK<T> S = make_stepk<T>(dtd, dx, dy, g);
+    T added = T(0), speed = T(0);
+    double bw = 0.0, be = 0.0, bs = 0.0, bn = 0.0;
+    bool bad = false;
+    if (i < G.nx && j < G.ny) {
+        const size_t k = (size_t)j * G.pitch + i;
+        const T zc = z[k];
+        Cell<T> cs = ld(es, us, vs, z, k);
+        Cell<T> xs = (i + CX >= 0 && i + CX < G.nx) ? ld(es, us, vs, z, (size_t)((ptrdiff_t)k + CX))
+                                                   : ghost(cs, CX > 0 ? SIDE_E : SIDE_W, G);
+        Cell<T> ys = (j + CY >= 0 && j + CY < G.ny) ? ld(es, us, vs, z, (size_t)((ptrdiff_t)k + (ptrdiff_t)CY * G.pitch))
+                                                   : ghost(cs, CY > 0 ? SIDE_N : SIDE_S, G);
+        const T e0 = e[k], u0 = u[k], v0 = v[k];
+        T gn2 = n2 ? n2[k] : G.gn2;
+        T fe, fw, fn, fs;
+        const T qxs = (cs.e - cs.z) * cs.u, qys = (cs.e - cs.z) * cs.v;
+        faces<CX>(qxs, (xs.e - xs.z) * xs.u, i == 0, i == G.nx - 1, SIDE_W, SIDE_E, G, fe, fw);
+        faces<CY>(qys, (ys.e - ys.z) * ys.v, j == 0, j == G.ny - 1, SIDE_S, SIDE_N, G, fn, fs);
+        T eo, uo, vo;
+        stage<CX, CY>(cs, xs, ys, fe, fw, fn, fs, e0, u0, v0, gn2, S, G.h_dry, eo, uo, vo);
+        // S14: average
+        T en = T(0.5) * (cs.e + eo), un = T(0.5) * (cs.u + uo), vn = T(0.5) * (cs.v + vo);
+        // S15: dissipation of level n
+        if (G.kappa != T(0)) {
+            auto hat = [&](int ii, int jj) -> T {
+                ii = ii < 0 ? 0 : (ii >= G.nx ? G.nx - 1 : ii);
+                jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
+                size_t q = (size_t)jj * G.pitch + ii;
+                return e[q] - z[q];
+            };
+            auto at = [&](const T* f, int ii, int jj) -> T {
+                ii = ii < 0 ? 0 : (ii >= G.nx ? G.nx - 1 : ii);
+                jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
+                return f[(size_t)jj * G.pitch + ii];
+            };
+            const T hc = e0 - zc;
+            const T hxm2 = hat(i - 2, j), hxm1 = hat(i - 1, j), hxp1 = hat(i + 1, j), hxp2 = hat(i + 2, j);
+            const T hym2 = hat(i, j - 2), hym1 = hat(i, j - 1), hyp1 = hat(i, j + 1), hyp2 = hat(i, j + 2);
+            const T hd = G.h_dry;
+            const bool wc = hc > hd;
+            const T nxc = nu_switch(hxm1, hc, hxp1), nyc = nu_switch(hym1, hc, hyp1);
+            T ee = (i + 1 < G.nx && wc && hxp1 > hd) ? tmax(nxc, nu_switch(hc, hxp1, hxp2)) : T(0);
+            T ew = (i - 1 >= 0 && wc && hxm1 > hd) ? tmax(nu_switch(hxm2, hxm1, hc), nxc) : T(0);
+            T en2 = (j + 1 < G.ny && wc && hyp1 > hd) ? tmax(nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
+            T es2 = (j - 1 >= 0 && wc && hym1 > hd) ? tmax(nu_switch(hym2, hym1, hc), nyc) : T(0);
+            const T* f3[3] = {e, u, v};
+            T* o3[3] = {&en, &un, &vn};
+            const T c3[3] = {e0, u0, v0};
+            #pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T tx = ee * (at(f3[f], i + 1, j) - c3[f]) - ew * (c3[f] - at(f3[f], i - 1, j));
+                T ty = en2 * (at(f3[f], i, j + 1) - c3[f]) - es2 * (c3[f] - at(f3[f], i, j - 1));
+                *o3[f] = *o3[f] + G.kappa * (tx + ty);
+            }
+        }
+        // S16: fix, tallies
+        added = wetdry_fix(en, un, vn, zc, G.h_dry);
+        e1[k] = en; u1[k] = un; v1[k] = vn;
+        speed = cfl_speed(en, un, vn, zc, G);
+        bad = !isfinite(en + un + vn);
+        const T qxn = (e0 - zc) * u0, qyn = (e0 - zc) * v0;
+        if (i == 0) bw = 0.5 * ((double)face_bnd(SIDE_W, qxn, G) + (double)face_bnd(SIDE_W, qxs, G));
+        if (i == G.nx - 1) be = -0.5 * ((double)face_bnd(SIDE_E, qxn, G) + (double)face_bnd(SIDE_E, qxs, G));
+        if (j == 0) bs = 0.5 * ((double)face_bnd(SIDE_S, qyn, G) + (double)face_bnd(SIDE_S, qys, G));
+        if (j == G.ny - 1) bn = -0.5 * ((double)face_bnd(SIDE_N, qyn, G) + (double)face_bnd(SIDE_N, qys, G));
+    }
+    const int lane = threadIdx.x & 31;
+    T m = warp_max(speed);
+    if (lane == 0 && m > T(0))
+        atomicMax(&ctl->smax[slot_next], (unsigned long long)__double_as_longlong((double)m));
+    if (__any_sync(0xffffffffu, added != T(0))) {
+        double s = warp_sum((double)added);
+        if (lane == 0 && s != 0.0) atomicAdd(&ctl->clamp, s * area);
+    }
+    if (__any_sync(0xffffffffu, bw != 0.0 || be != 0.0 || bs != 0.0 || bn != 0.0)) {
+        double a = warp_sum(bw), b = warp_sum(be), c2 = warp_sum(bs), d = warp_sum(bn);
+        if (lane == 0) {
+            if (a != 0.0) atomicAdd(&ctl->bflux[0], a * dtd * dy);
+            if (b != 0.0) atomicAdd(&ctl->bflux[1], b * dtd * dy);
+            if (c2 != 0.0) atomicAdd(&ctl->bflux[2], c2 * dtd * dx);
+            if (d != 0.0) atomicAdd(&ctl->bflux[3], d * dtd * dx);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->flags, (unsigned)SWE_FLAG_NONFINITE);
+}
+
+template <class T>
+static GridK<T> grid_of(const swe_ctx* c) {
+    GridK<T> G;
+    const swe_params& p = c->p;
+    G.nx = p.nx; G.ny = p.ny; G.pitch = c->pitch;
+    G.g = (T)p.g; G.h_dry = (T)p.h_dry; G.kappa = (T)p.kappa;
+    G.gn2 = (T)(p.g * p.manning_n * p.manning_n);
+    G.inv_dx = (T)(1.0 / p.dx); G.inv_dy = (T)(1.0 / p.dy);
+    for (int s = 0; s < 4; ++s) { G.bc[s] = p.bc[s]; G.qin[s] = (T)p.q_in[s]; }
+    return G;
+}
+
+template <class T, int SX, int SY>
+static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
+    const swe_params& p = c->p;
+    GridK<T> G = grid_of<T>(c);
+    int slot = (int)(k % 3), slot_next = (int)((k + 1) % 3);
+    k_plain_dt<<<1, 1, 0, c->stream>>>(c->ctl, slot, slot_next, c->dt_fixed_cap > 0 && c->dt_fixed ? c->dt_fixed : nullptr,
+                                       s, c->dt_hist, p.cfl, p.dt_max);
+    dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
+    const int a = c->cur, b = 1 - c->cur;
+    const double area = p.dx * p.dy;
+    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(
+        G, c->ctl, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        (const T*)c->n2, (T*)c->ps[0], (T*)c->ps[1], (T*)c->ps[2], c->ctl, area);
+    k_plain_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(
+        G, c->ctl, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        (const T*)c->n2, (const T*)c->ps[0], (const T*)c->ps[1], (const T*)c->ps[2], (T*)c->eta[b], (T*)c->u[b],
+        (T*)c->v[b], slot_next, area);
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t plain_step_dir(swe_ctx* c, int s, long long k) {
+    int sx, sy;
+    step_dirs(c->p.dir_cycle, k, &sx, &sy);
+    if (sx > 0 && sy > 0) return plain_step_t<T, 1, 1>(c, s, k);
+    if (sx > 0 && sy < 0) return plain_step_t<T, 1, -1>(c, s, k);
+    if (sx < 0 && sy > 0) return plain_step_t<T, -1, 1>(c, s, k);
+    return plain_step_t<T, -1, -1>(c, s, k);
+}
+
+// ---------------------------------------------------------------- utilities
+template <class T>
+__global__ void k_to_real(const double* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
+                          double scale_sq) {
+    size_t n = (size_t)pitch * ny;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(q / pitch), i = (int)(q % pitch);
+        double x = (i < nx) ? src[(size_t)j * nx + i] : 0.0;
+        if (scale_sq != 0.0) x = scale_sq * x * x;
+        dst[q] = (T)x;
+    }
+}
+
+template <class T>
+__global__ void k_to_double(const T* __restrict__ src, double* __restrict__ dst, int nx, int ny, int pitch) {
+    size_t n = (size_t)nx * ny;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(q / nx), i = (int)(q % nx);
+        dst[q] = (double)src[(size_t)j * pitch + i];
+    }
+}
+
+template <class T>
+__global__ void k_dense_copy(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
+                             int to_pitched) {
+    size_t n = (size_t)nx * ny;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(q / nx), i = (int)(q % nx);
+        size_t pq = (size_t)j * pitch + i;
+        if (to_pitched) dst[pq] = src[q]; else dst[q] = src[pq];
+    }
+}
+
+// Set-state normalisation on the context's real type: reject non-finite
+// values and depths below -1e-12 m (bad bits 1 and 2), clamp small negative
+// depths to zero and zero the velocity of dry cells.
+template <class T>
+__global__ void k_normalise(T* e, T* u, T* v, const T* z, int nx, int ny, int pitch, T h_dry,
+                            unsigned int* bad) {
+    size_t n = (size_t)nx * ny;
+    unsigned int b = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        size_t k = (q / nx) * (size_t)pitch + q % nx;
+        T ee = e[k], uu = u[k], vv = v[k], zz = z[k];
+        if (!isfinite(ee) || !isfinite(uu) || !isfinite(vv) || !isfinite(zz)) { b |= 1u; continue; }
+        T h = ee - zz;
+        if (h < T(-1e-12)) { b |= 2u; continue; }
+        if (h < T(0)) { ee = zz; h = T(0); }
+        if (h <= h_dry) { uu = T(0); vv = T(0); }
+        e[k] = ee; u[k] = uu; v[k] = vv;
+    }
+    if (b) atomicOr(bad, b);
+}
+
+// The same normalisation in FP64 on dense staging planes (eta, u, v) against
+// the FP64 bed, before the state is rounded to the context's real type.
+__global__ void k_normalise64(double* st, const double* z64, size_t n, double h_dry, unsigned int* bad) {
+    unsigned int b = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        double ee = st[q], uu = st[n + q], vv = st[2 * n + q], zz = z64[q];
+        if (!isfinite(ee) || !isfinite(uu) || !isfinite(vv) || !isfinite(zz)) { b |= 1u; continue; }
+        double h = ee - zz;
+        if (h < -1e-12) { b |= 2u; continue; }
+        if (h < 0.0) { ee = zz; h = 0.0; }
+        if (h <= h_dry) { uu = 0.0; vv = 0.0; }
+        st[q] = ee; st[n + q] = uu; st[2 * n + q] = vv;
+    }
+    if (b) atomicOr(bad, b);
+}
+
+// CFL reduction of a freshly set state into slot `slot`; the other slots
+// are cleared.
+template <class T>
+__global__ void k_prologue(GridK<T> G, const T* e, const T* u, const T* v, const T* z, DevCtl* ctl, int slot) {
+    size_t n = (size_t)G.nx * G.ny;
+    T m = T(0);
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        size_t k = (q / G.nx) * (size_t)G.pitch + q % G.nx;
+        T s = cfl_speed(e[k], u[k], v[k], z[k], G);
+        m = s > m ? s : m;
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0 && m > T(0))
+        atomicMax(&ctl->smax[slot], (unsigned long long)__double_as_longlong((double)m));
+}
+
+// Diagnostics: per-block FP64 partial volume (fixed row ranges, fixed order)
+// and wet count, then one block sums the partials in order.
+template <class T>
+__global__ void k_diag_part(GridK<T> G, const T* e, const T* u, const T* v, const T* z, double* part,
+                            long long* wet, unsigned int* bad, int rows_per_block) {
+    __shared__ double sh[32];
+    __shared__ long long shw[32];
+    const int j0 = blockIdx.x * rows_per_block, j1 = min(G.ny, j0 + rows_per_block);
+    double s = 0.0;
+    long long w = 0;
+    unsigned int b = 0;
+    for (int j = j0; j < j1; ++j)
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
+            size_t k = (size_t)j * G.pitch + i;
+            double h = (double)e[k] - (double)z[k];
+            s += h;
+            w += (T)(e[k] - z[k]) > G.h_dry;
+            if (!isfinite(e[k]) || !isfinite(u[k]) || !isfinite(v[k])) b = 1;
+        }
+    s = warp_sum(s);
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[wid] = s; shw[wid] = w; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        long long tw = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { t += sh[q]; tw += shw[q]; }
+        part[blockIdx.x] = t;
+        wet[blockIdx.x] = tw;
+    }
+    if (b) atomicOr(bad, 1u);
+}
+
+__global__ void k_diag_final(const double* part, const long long* wet, int nparts, DevDiag* out, double area,
+                             const unsigned int* bad) {
+    double t = 0.0;
+    long long w = 0;
+    for (int q = 0; q < nparts; ++q) { t += part[q]; w += wet[q]; }
+    out->volume = t * area;
+    out->n_wet = w;
+    out->nonfinite = *bad;
+}
+
+__global__ void k_call_begin(DevCtl* ctl) {
+    ctl->dt_min = 1e300;
+    ctl->dt_maxs = 0.0;
+    ctl->flags = 0u;
+}
+
+}  // namespace swe
+
+using namespace swe;
+
+static int util_blocks(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+cudaError_t swe_launch_plain_step(swe_ctx* c, int s, long long k) {
+    if (c->real_size == 8) return plain_step_dir<double>(c, s, k);
+    return plain_step_dir<float>(c, s, k);
+}
+
+cudaError_t swe_launch_to_real(swe_ctx* c, const double* src, void* dst, int n_planes, bool square_n) {
+    size_t n = c->plane;
+    double scale = square_n ? c->p.g : 0.0;
+    for (int pl = 0; pl < n_planes; ++pl) {
+        const double* s = src + (size_t)pl * c->p.nx * c->p.ny;
+        if (c->real_size == 8)
+            k_to_real<double><<<util_blocks(n), 256, 0, c->stream>>>(s, (double*)dst + pl * n, c->p.nx, c->p.ny, c->pitch, scale);
+        else
+            k_to_real<float><<<util_blocks(n), 256, 0, c->stream>>>(s, (float*)dst + pl * n, c->p.nx, c->p.ny, c->pitch, scale);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_to_double(swe_ctx* c, const void* src, double* dst) {
+    size_t n = (size_t)c->p.nx * c->p.ny;
+    if (c->real_size == 8)
+        k_to_double<double><<<util_blocks(n), 256, 0, c->stream>>>((const double*)src, dst, c->p.nx, c->p.ny, c->pitch);
+    else
+        k_to_double<float><<<util_blocks(n), 256, 0, c->stream>>>((const float*)src, dst, c->p.nx, c->p.ny, c->pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_dense_copy(swe_ctx* c, const void* src, void* dst, bool to_pitched) {
+    size_t n = (size_t)c->p.nx * c->p.ny;
+    if (c->real_size == 8)
+        k_dense_copy<double><<<util_blocks(n), 256, 0, c->stream>>>((const double*)src, (double*)dst, c->p.nx, c->p.ny, c->pitch, to_pitched);
+    else
+        k_dense_copy<float><<<util_blocks(n), 256, 0, c->stream>>>((const float*)src, (float*)dst, c->p.nx, c->p.ny, c->pitch, to_pitched);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_normalise(swe_ctx* c, unsigned int* bad) {
+    size_t n = (size_t)c->p.nx * c->p.ny;
+    int a = c->cur;
+    if (c->real_size == 8)
+        k_normalise<double><<<util_blocks(n), 256, 0, c->stream>>>((double*)c->eta[a], (double*)c->u[a], (double*)c->v[a],
+                                                                  (const double*)c->z, c->p.nx, c->p.ny, c->pitch, c->p.h_dry, bad);
+    else
+        k_normalise<float><<<util_blocks(n), 256, 0, c->stream>>>((float*)c->eta[a], (float*)c->u[a], (float*)c->v[a],
+                                                                 (const float*)c->z, c->p.nx, c->p.ny, c->pitch, (float)c->p.h_dry, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_normalise64(swe_ctx* c, double* stage, unsigned int* bad) {
+    size_t n = (size_t)c->p.nx * c->p.ny;
+    k_normalise64<<<util_blocks(n), 256, 0, c->stream>>>(stage, c->z64, n, c->p.h_dry, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_prologue(swe_ctx* c) {
+    size_t n = (size_t)c->p.nx * c->p.ny;
+    int a = c->cur;
+    int slot = (int)(c->step % 3);
+    cudaError_t e = cudaMemsetAsync(c->ctl->smax, 0, sizeof(c->ctl->smax), c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->real_size == 8)
+        k_prologue<double><<<util_blocks(n), 256, 0, c->stream>>>(grid_of<double>(c), (const double*)c->eta[a], (const double*)c->u[a],
+                                                                 (const double*)c->v[a], (const double*)c->z, c->ctl, slot);
+    else
+        k_prologue<float><<<util_blocks(n), 256, 0, c->stream>>>(grid_of<float>(c), (const float*)c->eta[a], (const float*)c->u[a],
+                                                                (const float*)c->v[a], (const float*)c->z, c->ctl, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_diag(swe_ctx* c) {
+    int a = c->cur;
+    int rpb = (c->p.ny + c->diag_blocks - 1) / c->diag_blocks;
+    int nb = (c->p.ny + rpb - 1) / rpb;
+    cudaError_t e = cudaMemsetAsync(c->diag_bad, 0, sizeof(unsigned int), c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->real_size == 8)
+        k_diag_part<double><<<nb, 256, 0, c->stream>>>(grid_of<double>(c), (const double*)c->eta[a], (const double*)c->u[a],
+                                                        (const double*)c->v[a], (const double*)c->z, c->diag_part, c->diag_wet,
+                                                        c->diag_bad, rpb);
+    else
+        k_diag_part<float><<<nb, 256, 0, c->stream>>>(grid_of<float>(c), (const float*)c->eta[a], (const float*)c->u[a],
+                                                       (const float*)c->v[a], (const float*)c->z, c->diag_part, c->diag_wet,
+                                                       c->diag_bad, rpb);
+    k_diag_final<<<1, 1, 0, c->stream>>>(c->diag_part, c->diag_wet, nb, c->diag, c->p.dx * c->p.dy, c->diag_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t swe_launch_call_begin(swe_ctx* c) {
+    k_call_begin<<<1, 1, 0, c->stream>>>(c->ctl);
+    return cudaGetLastError();
+}

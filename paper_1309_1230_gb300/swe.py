@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in ``include/swe.h``.
+
+Argument marshalling only: every step of the scheme runs in the CUDA library
+``libswe.so``.  There is no other implementation behind these names; if the
+library is missing or cannot load, every call raises.
+
+The functions keep the C names (``swe_create``, ``swe_set_bed``,
+``swe_set_state``, ``swe_step``, ``swe_get_state``, ``swe_destroy``, ...).
+``Solver`` is a small convenience wrapper over them for numpy and torch
+arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+SWE_OK, SWE_ERR_ARG, SWE_ERR_CUDA, SWE_ERR_NONFINITE = 0, 1, 2, 3
+SWE_ERR_NEGDEPTH, SWE_ERR_TIMEOUT, SWE_ERR_STATE, SWE_ERR_UNSUPPORTED = 4, 5, 6, 7
+SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_OUTFLOW = 0, 1, 2
+SWE_FP64, SWE_FP32 = 0, 1
+SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN = 0, 1
+SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED = 1, 2, 4
+
+
+class swe_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("g", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("h_dry", ctypes.c_double), ("dt_max", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("manning_n", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4), ("q_in", ctypes.c_double * 4),
+        ("precision", ctypes.c_int32), ("dir_cycle", ctypes.c_int32),
+        ("device", ctypes.c_int32), ("kernel", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("seg_rows", ctypes.c_int32), ("cta_warps", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32), ("dry_skip", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
+    ]
+
+
+class swe_step_info(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("dt_last", ctypes.c_double),
+        ("dt_min", ctypes.c_double), ("dt_max_seen", ctypes.c_double),
+        ("volume", ctypes.c_double), ("clamp_volume", ctypes.c_double),
+        ("bflux", ctypes.c_double * 4),
+        ("step", ctypes.c_int64), ("n_wet", ctypes.c_int64),
+        ("flags", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_ctxp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "swe_params_default": (None, [ctypes.POINTER(swe_params)]),
+    "swe_create": (ctypes.c_int, [ctypes.POINTER(swe_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "swe_set_bed": (ctypes.c_int, [_ctxp, _dp, _dp]),
+    "swe_set_state": (ctypes.c_int, [_ctxp, _dp, _dp, _dp]),
+    "swe_set_clock": (ctypes.c_int, [_ctxp, ctypes.c_int64, ctypes.c_double]),
+    "swe_step": (ctypes.c_int, [_ctxp, ctypes.c_int32, _dp, _dp, ctypes.POINTER(swe_step_info)]),
+    "swe_get_state": (ctypes.c_int, [_ctxp, _dp, _dp, _dp]),
+    "swe_get_info": (ctypes.c_int, [_ctxp, ctypes.POINTER(swe_step_info)]),
+    "swe_set_state_device": (ctypes.c_int, [_ctxp, _vp, _vp, _vp]),
+    "swe_get_state_device": (ctypes.c_int, [_ctxp, _vp, _vp, _vp]),
+    "swe_set_bed_device": (ctypes.c_int, [_ctxp, _vp, _vp]),
+    "swe_stream": (ctypes.c_void_p, [_ctxp]),
+    "swe_destroy": (None, [_ctxp]),
+    "swe_last_error": (ctypes.c_char_p, [_ctxp]),
+    "swe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libswe.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run the build first")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class SweError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(st: int, ctx=None):
+    if st != SWE_OK:
+        lib = load()
+        text = lib.swe_last_error(ctx).decode() if ctx else lib.swe_status_string(st).decode()
+        raise SweError(st, text or lib.swe_status_string(st).decode())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def make_params(nx, ny, *, dx=1.0, dy=1.0, g=9.81, cfl=0.5, h_dry=1e-3, dt_max=10.0, kappa=0.0,
+                manning_n=0.0, bc=(0, 0, 0, 0), q_in=(0.0, 0.0, 0.0, 0.0), precision=SWE_FP64,
+                dir_cycle=1, device=0, kernel=SWE_KERNEL_FUSED, stream=None, seg_rows=0, cta_warps=0,
+                use_graph=1, dry_skip=1) -> swe_params:
+    p = swe_params()
+    load().swe_params_default(ctypes.byref(p))
+    p.nx, p.ny, p.dx, p.dy, p.g, p.cfl = int(nx), int(ny), dx, dy, g, cfl
+    p.h_dry, p.dt_max, p.kappa, p.manning_n = h_dry, dt_max, kappa, manning_n
+    for s in range(4):
+        p.bc[s] = int(bc[s])
+        p.q_in[s] = float(q_in[s])
+    p.precision, p.dir_cycle, p.device, p.kernel = int(precision), int(dir_cycle), int(device), int(kernel)
+    p.stream = stream
+    p.seg_rows, p.cta_warps, p.use_graph, p.dry_skip = int(seg_rows), int(cta_warps), int(use_graph), int(dry_skip)
+    return p
+
+
+@dataclass
+class StepInfo:
+    t: float
+    dt_last: float
+    dt_min: float
+    dt_max_seen: float
+    volume: float
+    clamp_volume: float
+    bflux: tuple
+    step: int
+    n_wet: int
+    flags: int
+
+
+def _info(i: swe_step_info) -> StepInfo:
+    return StepInfo(i.t, i.dt_last, i.dt_min, i.dt_max_seen, i.volume, i.clamp_volume, tuple(i.bflux),
+                    int(i.step), int(i.n_wet), int(i.flags))
+
+
+class Solver:
+    """One grid on one GPU: owns a swe_ctx."""
+
+    def __init__(self, nx, ny, **kw):
+        self.lib = load()
+        self.params = make_params(nx, ny, **kw)
+        self.nx, self.ny = int(nx), int(ny)
+        ctx = ctypes.c_void_p()
+        st = self.lib.swe_create(ctypes.byref(self.params), ctypes.byref(ctx))
+        if st != SWE_OK:
+            raise SweError(st, "swe_create failed: " + self.lib.swe_status_string(st).decode())
+        self.ctx = ctx
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.swe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_bed(self, z, n_field=None):
+        z = _f64(z, self.shape)
+        nf = None if n_field is None else _f64(n_field, self.shape)
+        _check(self.lib.swe_set_bed(self.ctx, _p(z), _p(nf)), self.ctx)
+
+    def set_state(self, eta, u, v):
+        e, uu, vv = (_f64(a, self.shape) for a in (eta, u, v))
+        _check(self.lib.swe_set_state(self.ctx, _p(e), _p(uu), _p(vv)), self.ctx)
+
+    def set_clock(self, step: int, t: float):
+        _check(self.lib.swe_set_clock(self.ctx, int(step), float(t)), self.ctx)
+
+    def step(self, nsteps: int, dt_fixed=None, want_dt: bool = False, want_info: bool = True):
+        dtf = None
+        if dt_fixed is not None:
+            dtf = np.ascontiguousarray(dt_fixed, dtype=np.float64)
+            if dtf.shape != (nsteps,):
+                raise ValueError("dt_fixed must hold nsteps values")
+        dto = np.zeros(max(1, nsteps), dtype=np.float64) if want_dt else None
+        info = swe_step_info()
+        st = self.lib.swe_step(self.ctx, int(nsteps), _p(dtf), _p(dto),
+                               ctypes.byref(info) if want_info else None)
+        _check(st, self.ctx)
+        out = _info(info) if want_info else None
+        if want_dt:
+            return out, dto[:nsteps]
+        return out
+
+    def get_state(self):
+        e = np.empty(self.shape)
+        u = np.empty(self.shape)
+        v = np.empty(self.shape)
+        _check(self.lib.swe_get_state(self.ctx, _p(e), _p(u), _p(v)), self.ctx)
+        return e, u, v
+
+    def info(self) -> StepInfo:
+        i = swe_step_info()
+        _check(self.lib.swe_get_info(self.ctx, ctypes.byref(i)), self.ctx)
+        return _info(i)
+
+    # torch tensors on the context's device, of the context's real type
+    def set_state_device(self, eta, u, v):
+        for a in (eta, u, v):
+            _torch_check(a, self)
+        _check(self.lib.swe_set_state_device(self.ctx, eta.data_ptr(), u.data_ptr(), v.data_ptr()), self.ctx)
+
+    def get_state_device(self, eta, u, v):
+        for a in (eta, u, v):
+            _torch_check(a, self)
+        _check(self.lib.swe_get_state_device(self.ctx, eta.data_ptr(), u.data_ptr(), v.data_ptr()), self.ctx)
+
+    def stream_handle(self) -> int:
+        return int(self.lib.swe_stream(self.ctx) or 0)
+
+
+def _torch_check(a, s: Solver):
+    import torch
+    want = torch.float64 if s.params.precision == SWE_FP64 else torch.float32
+    if not (a.is_cuda and a.dtype == want and a.is_contiguous() and tuple(a.shape) == s.shape):
+        raise ValueError(f"expected a contiguous CUDA {want} tensor of shape {s.shape}")
