@@ -20,10 +20,12 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# FP32 arithmetic uses approximate division/square root with flush-to-zero;
-# these flags do not touch FP64, which stays IEEE.
+# FP32 arithmetic uses approximate division/square root with flush-to-zero
+# (these flags do not touch FP64, which stays IEEE).  No implicit multiply-add
+# contraction: the kernels write their FMAs out, so every kernel form rounds a
+# cell identically.
 NVFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
-                  "-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-fmad=true",
+                  "-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-fmad=false",
                   "-I", INCLUDE]
 
 

@@ -64,7 +64,7 @@ void free_all(swe_ctx* c, F&& f) {
     f(c->z); f(c->z64); f(c->n2);
     for (int q = 0; q < 3; ++q) f(c->ps[q]);
     f(c->ctl); f(c->diag); f(c->diag_part); f(c->diag_wet); f(c->diag_bad);
-    f(c->dt_hist); f(c->dt_fixed); f(c->stage); f(c->seg_same); f(c->tmaps); f(c->bad_flag);
+    f(c->dt_hist); f(c->dt_fixed); f(c->stage); f(c->seg_same); f(c->bad_flag);
 }
 
 swe_status ensure_stage(swe_ctx* c, size_t elems) {
@@ -169,6 +169,7 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
         free_all(c, [](void* q) { if (q) cudaFree(q); });
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         if (c->h_ctl) cudaFreeHost(c->h_ctl);
+        free(c->tmaps);
         delete c;
         return SWE_ERR_CUDA;
     };
@@ -223,6 +224,7 @@ void swe_destroy(swe_ctx* c) {
     free_all(c, [](void* q) { if (q) cudaFree(q); });
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    free(c->tmaps);  // host-side work plan
     delete c;
 }
 

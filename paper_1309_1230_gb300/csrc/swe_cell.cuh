@@ -7,7 +7,9 @@
 //
 // Real type T is float (FP32 form) or double (FP64 form).  In FP32 the
 // translation unit is compiled with approximate division/square root and
-// flush-to-zero; FP64 is IEEE throughout.
+// flush-to-zero; FP64 is IEEE throughout.  The library is compiled without
+// implicit multiply-add contraction: every fused multiply-add below is
+// written out (fma_), so the rounding of a cell is fixed by this file alone.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -52,6 +54,13 @@ __host__ __device__ inline StepK<T> make_stepk(double dt, double dx, double dy, 
     s.g_dtdy = (T)(g * dt / dy);
     return s;
 }
+
+template <class T>
+__device__ __forceinline__ T fma_(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 __device__ __forceinline__ float pow_m43(float h) { return __powf(h, -1.33333333f); }
 __device__ __forceinline__ double pow_m43(double h) {
@@ -119,7 +128,7 @@ __device__ __forceinline__ void faces(T qc, T qn, bool lo, bool hi, int side_lo,
 template <class T>
 __device__ __forceinline__ T friction(const Cell<T>& c, T gn2, T h_dry) {
     T h = c.e - c.z;
-    T s2 = c.u * c.u + c.v * c.v;
+    T s2 = fma_(c.u, c.u, c.v * c.v);
     T mag = s2 > T(0) ? rsq_sqrt(s2) : T(0);
     return (h > h_dry) ? gn2 * mag * pow_m43(h) : T(0);
 }
@@ -133,7 +142,7 @@ template <int DX, int DY, class T>
 __device__ __forceinline__ void stage(const Cell<T>& c, const Cell<T>& xn, const Cell<T>& yn,
                                       T fe, T fw, T fn, T fs, T e0, T u0, T v0, T gn2,
                                       const StepK<T>& S, T h_dry, T& eo, T& uo, T& vo) {
-    eo = e0 - (S.dtdx * (fe - fw) + S.dtdy * (fn - fs));
+    eo = e0 - fma_(S.dtdx, fe - fw, S.dtdy * (fn - fs));
     T cf = friction(c, gn2, h_dry);
     T ex = eta_seen(xn, c.e, h_dry);
     T ey = eta_seen(yn, c.e, h_dry);
@@ -142,9 +151,9 @@ __device__ __forceinline__ void stage(const Cell<T>& c, const Cell<T>& xn, const
     else        { dux = c.u - xn.u; dvx = c.v - xn.v; dex = c.e - ex; }
     if (DY > 0) { duy = yn.u - c.u; dvy = yn.v - c.v; dey = ey - c.e; }
     else        { duy = c.u - yn.u; dvy = c.v - yn.v; dey = c.e - ey; }
-    T au = c.u * (S.dtdx * dux) + c.v * (S.dtdy * duy) + S.g_dtdx * dex;
-    T av = c.u * (S.dtdx * dvx) + c.v * (S.dtdy * dvy) + S.g_dtdy * dey;
-    T r = T(1) / (T(1) + S.dt * cf);
+    T au = fma_(c.u, S.dtdx * dux, fma_(c.v, S.dtdy * duy, S.g_dtdx * dex));
+    T av = fma_(c.u, S.dtdx * dvx, fma_(c.v, S.dtdy * dvy, S.g_dtdy * dey));
+    T r = T(1) / fma_(S.dt, cf, T(1));
     uo = (u0 - au) * r;
     vo = (v0 - av) * r;
 }
@@ -163,9 +172,24 @@ __device__ __forceinline__ T wetdry_fix(T& e, T& u, T& v, T z, T h_dry) {
 // Dissipation switch of a cell along one axis (S15).
 template <class T>
 __device__ __forceinline__ T nu_switch(T hl, T hc, T hr) {
-    T num = fabs((hl + hr) - T(2) * hc);
-    T den = (fabs(hl) + fabs(hr)) + T(2) * fabs(hc) + T(SWE_NU_TINY);
+    T num = fabs(fma_(T(-2), hc, hl + hr));
+    T den = fma_(T(2), fabs(hc), fabs(hl) + fabs(hr)) + T(SWE_NU_TINY);
     return num / den;
+}
+
+// Face coefficient of the dissipation: interior face between two wet cells.
+template <class T>
+__device__ __forceinline__ T face_eps(bool wet_a, bool wet_b, T nu_a, T nu_b) {
+    return (wet_a && wet_b) ? tmax(nu_a, nu_b) : T(0);
+}
+
+// S15 for one field of a cell: out + kappa * (x term + y term) with the
+// level-n values c (cell), l/r (x neighbours), b/t (y neighbours).
+template <class T>
+__device__ __forceinline__ T dissip(T out, T c, T l, T r, T b, T t, T ee, T ew, T en, T es, T kappa) {
+    T tx = fma_(ee, r - c, -(ew * (c - l)));
+    T ty = fma_(en, t - c, -(es * (c - b)));
+    return fma_(kappa, tx + ty, out);
 }
 
 // CFL speed of a cell (S2); 0 for dry cells.
@@ -174,7 +198,7 @@ __device__ __forceinline__ T cfl_speed(T e, T u, T v, T z, const GridK<T>& G) {
     T h = e - z;
     if (!(h > G.h_dry)) return T(0);
     T c = rsq_sqrt(G.g * h);
-    return (fabs(u) + c) * G.inv_dx + (fabs(v) + c) * G.inv_dy;
+    return fma_(fabs(u) + c, G.inv_dx, (fabs(v) + c) * G.inv_dy);
 }
 
 // Step size from the reduced CFL speed (S2), FP64.

@@ -1,0 +1,12 @@
+// swe_fused_f64_0.cu -- instantiation of the fused step for FP64 without dissipation.
+#include "swe_fused.cuh"
+
+namespace swe {
+namespace fz {
+
+cudaError_t launch_f64_0(swe_ctx* c, const Plan& pl, int s, long long k) {
+    return launch_dir<double, 2, false>(c, pl, s, k);
+}
+
+}  // namespace fz
+}  // namespace swe

@@ -133,19 +133,13 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, dou
             const T hd = G.h_dry;
             const bool wc = hc > hd;
             const T nxc = nu_switch(hxm1, hc, hxp1), nyc = nu_switch(hym1, hc, hyp1);
-            T ee = (i + 1 < G.nx && wc && hxp1 > hd) ? tmax(nxc, nu_switch(hc, hxp1, hxp2)) : T(0);
-            T ew = (i - 1 >= 0 && wc && hxm1 > hd) ? tmax(nu_switch(hxm2, hxm1, hc), nxc) : T(0);
-            T en2 = (j + 1 < G.ny && wc && hyp1 > hd) ? tmax(nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
-            T es2 = (j - 1 >= 0 && wc && hym1 > hd) ? tmax(nu_switch(hym2, hym1, hc), nyc) : T(0);
-            const T* f3[3] = {e, u, v};
-            T* o3[3] = {&en, &un, &vn};
-            const T c3[3] = {e0, u0, v0};
-            #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                T tx = ee * (at(f3[f], i + 1, j) - c3[f]) - ew * (c3[f] - at(f3[f], i - 1, j));
-                T ty = en2 * (at(f3[f], i, j + 1) - c3[f]) - es2 * (c3[f] - at(f3[f], i, j - 1));
-                *o3[f] = *o3[f] + G.kappa * (tx + ty);
-            }
+            T ee = (i + 1 < G.nx) ? face_eps(wc, hxp1 > hd, nxc, nu_switch(hc, hxp1, hxp2)) : T(0);
+            T ew = (i - 1 >= 0) ? face_eps(hxm1 > hd, wc, nu_switch(hxm2, hxm1, hc), nxc) : T(0);
+            T en2 = (j + 1 < G.ny) ? face_eps(wc, hyp1 > hd, nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
+            T es2 = (j - 1 >= 0) ? face_eps(hym1 > hd, wc, nu_switch(hym2, hym1, hc), nyc) : T(0);
+            en = dissip(en, e0, at(e, i - 1, j), at(e, i + 1, j), at(e, i, j - 1), at(e, i, j + 1), ee, ew, en2, es2, G.kappa);
+            un = dissip(un, u0, at(u, i - 1, j), at(u, i + 1, j), at(u, i, j - 1), at(u, i, j + 1), ee, ew, en2, es2, G.kappa);
+            vn = dissip(vn, v0, at(v, i - 1, j), at(v, i + 1, j), at(v, i, j - 1), at(v, i, j + 1), ee, ew, en2, es2, G.kappa);
         }
         // S16: fix, tallies
         added = wetdry_fix(en, un, vn, zc, G.h_dry);

@@ -27,7 +27,7 @@ def gpu_solver(case, precision, kernel, **kw):
 
 def rel_depth_err(h_gpu, h_ref):
     """max |h - h_ref| / max h_ref and the L2 analogue."""
-    scale = float(np.max(np.abs(h_ref)))
+    scale = max(float(np.max(np.abs(h_ref))), 1e-3)  # floor: the wet/dry threshold
     d = h_gpu - h_ref
     return float(np.max(np.abs(d))) / scale, float(np.sqrt(np.mean(d * d))) / scale
 

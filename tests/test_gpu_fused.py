@@ -1,0 +1,172 @@
+"""GPU parity of the fused one-sweep step against the FP64 oracle, and the
+determinism the paper relies on (Sec. 1: cells may be solved in any order
+and the result stays deterministic): the fused result does not change with
+the work decomposition, and equals the plain one-thread-per-cell kernel.
+
+Tolerances as in test_gpu_plain.py: FP64 1e-10 of the field scale, FP32
+1e-4 relative in depth; decomposition changes are bitwise.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1309_1230_gb300 import inputs as I
+from tests.gpu_util import gpu_solver, oracle_params, rel_depth_err, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "basin": (lambda: I.basin_hump(64, 64, manning_n=0.03, kappa=0.0), 200),
+    "basin_k": (lambda: I.basin_hump(64, 64, manning_n=0.03, kappa=0.25), 200),
+    "river": (lambda: I.river(300, 70, seed=7), 300),
+    "dambreak": (lambda: I.dam_break(260, 90, seed=3), 300),
+    "ragged": (lambda: I.dam_break(37, 23, seed=11), 150),
+    "tall": (lambda: I.dam_break(9, 140, seed=12), 100),
+}
+
+
+def _run(case, precision, kernel, steps, dt_fixed=None, **kw):
+    s = gpu_solver(case, precision, kernel, **kw)
+    info, dts = s.step(steps, dt_fixed=dt_fixed, want_dt=True)
+    e, u, v = s.get_state()
+    s.close()
+    return info, dts, e, u, v
+
+
+def _oracle(oracle, case, steps):
+    p = oracle_params(oracle, case)
+    e0, u0, v0 = oracle.prepare_state(p, case["z"], case["eta"], case["u"], case["v"])
+    ref = oracle.run(p, case["z"], e0, u0, v0, steps, nthreads=4)
+    assert ref.status == 0
+    return ref
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fused_fp64_matches_oracle(oracle, name):
+    from paper_1309_1230_gb300 import swe
+    build, steps = CASES[name]
+    case = build()
+    ref = _oracle(oracle, case, steps)
+    info, dts, e, u, v = _run(case, swe.SWE_FP64, swe.SWE_KERNEL_FUSED, steps)
+    z = case["z"]
+    assert rel_err(dts, ref.dt) <= 1e-10
+    assert rel_err(e - z, ref.eta - z) <= 1e-10
+    assert rel_err(u, ref.u, 1e-3) <= 1e-9 and rel_err(v, ref.v, 1e-3) <= 1e-9
+    assert info.clamp_volume == pytest.approx(ref.clamp_volume, rel=1e-8, abs=1e-9)
+    assert np.allclose(info.bflux, ref.bflux, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fused_fp32_matches_oracle(oracle, name):
+    from paper_1309_1230_gb300 import swe
+    build, steps = CASES[name]
+    case = build()
+    ref = _oracle(oracle, case, steps)
+    info, dts, e, u, v = _run(case, swe.SWE_FP32, swe.SWE_KERNEL_FUSED, steps)
+    emax, el2 = rel_depth_err(e - case["z"], ref.eta - case["z"])
+    assert emax <= 1e-4, (emax, el2)
+    assert rel_err(dts, ref.dt) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["dambreak", "river", "ragged", "tall"])
+def test_fused_independent_of_decomposition(name, precision):
+    """Bitwise identical state for different rows-per-item, and equal to the
+    plain kernel."""
+    from paper_1309_1230_gb300 import swe
+    build, steps = CASES[name]
+    case = build()
+    steps = min(steps, 120)
+    runs = [_run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=L) for L in (0, 16, 37)]
+    plain = _run(case, precision, swe.SWE_KERNEL_PLAIN, steps)
+    for r in runs[1:] + [plain]:
+        assert np.array_equal(r[1], runs[0][1])
+        for a, b in zip(r[2:], runs[0][2:]):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (9, 1), (3, 3), (130, 5), (5, 130), (125, 4), (124, 3)])
+def test_fused_small_and_degenerate_grids(oracle, shape):
+    from paper_1309_1230_gb300 import swe
+    nx, ny = shape
+    case = I.dam_break(nx, ny, seed=nx * 1000 + ny, n_bumps=4)
+    steps = 30
+    ref = _oracle(oracle, case, steps)
+    for prec, tol in ((swe.SWE_FP64, 1e-10), (swe.SWE_FP32, 1e-4)):
+        info, dts, e, u, v = _run(case, prec, swe.SWE_KERNEL_FUSED, steps)
+        emax, _ = rel_depth_err(e - case["z"], ref.eta - case["z"])
+        assert emax <= tol, (prec, emax)
+
+
+def test_fused_lake_at_rest_bitwise():
+    from paper_1309_1230_gb300 import swe
+    rng = np.random.Generator(np.random.PCG64(11))
+    z = I.gaussian_sum_bed(300, 90, rng, 20, (0.0, 2.0), (3.0, 10.0))
+    eta = np.maximum(1.0, z)
+    zero = np.zeros_like(z)
+    case = dict(nx=300, ny=90, z=z, eta=eta, u=zero, v=zero, manning_n=0.03, kappa=0.25)
+    for prec in (swe.SWE_FP64, swe.SWE_FP32):
+        s = gpu_solver(case, prec, swe.SWE_KERNEL_FUSED)
+        e0, _, _ = s.get_state()
+        s.step(50)
+        e, u, v = s.get_state()
+        s.close()
+        assert np.array_equal(e, e0) and not u.any() and not v.any()
+
+
+def test_fused_per_cell_manning_field(oracle):
+    from paper_1309_1230_gb300 import swe
+    case = I.dam_break(200, 60, seed=21)
+    rng = np.random.Generator(np.random.PCG64(5))
+    case["nfield"] = 0.02 + 0.03 * rng.uniform(size=(60, 200))
+    steps = 100
+    p = oracle_params(oracle, case)
+    e0, u0, v0 = oracle.prepare_state(p, case["z"], case["eta"], case["u"], case["v"])
+    ref = oracle.run(p, case["z"], e0, u0, v0, steps, nfield=case["nfield"])
+    for prec, tol in ((swe.SWE_FP64, 1e-10), (swe.SWE_FP32, 1e-4)):
+        info, dts, e, u, v = _run(case, prec, swe.SWE_KERNEL_FUSED, steps)
+        emax, _ = rel_depth_err(e - case["z"], ref.eta - case["z"])
+        assert emax <= tol, (prec, emax)
+
+
+def test_fused_volume_and_resume():
+    """Closed basin volume is conserved; stepping 2 x 60 equals 120 steps
+    bitwise; get_state/set_state/set_clock resume bitwise."""
+    from paper_1309_1230_gb300 import swe
+    case = I.dam_break(180, 70, seed=9)
+    s = gpu_solver(case, swe.SWE_FP64, swe.SWE_KERNEL_FUSED)
+    v0 = s.info().volume
+    s.step(60)
+    mid = s.get_state()
+    mid_info = s.info()
+    s.step(60)
+    a = s.get_state()
+    info = s.info()
+    assert abs(info.volume - v0 - info.clamp_volume) <= 1e-11 * v0
+    s.close()
+    s2 = gpu_solver(case, swe.SWE_FP64, swe.SWE_KERNEL_FUSED)
+    s2.step(120)
+    b = s2.get_state()
+    s2.close()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    s3 = gpu_solver(case, swe.SWE_FP64, swe.SWE_KERNEL_FUSED)
+    s3.set_state(*mid)
+    s3.set_clock(mid_info.step, mid_info.t)
+    s3.step(60)
+    c = s3.get_state()
+    s3.close()
+    for x, y in zip(a, c):
+        assert np.array_equal(x, y)
+
+
+def test_fused_dt_replay(oracle):
+    from paper_1309_1230_gb300 import swe
+    build, steps = CASES["dambreak"]
+    case = build()
+    ref = _oracle(oracle, case, steps)
+    info, dts, e, u, v = _run(case, swe.SWE_FP32, swe.SWE_KERNEL_FUSED, steps, dt_fixed=ref.dt)
+    assert np.array_equal(dts, ref.dt)
+    emax, _ = rel_depth_err(e - case["z"], ref.eta - case["z"])
+    assert emax <= 1e-4
