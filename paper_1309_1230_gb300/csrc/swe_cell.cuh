@@ -183,13 +183,16 @@ __device__ __forceinline__ T face_eps(bool wet_a, bool wet_b, T nu_a, T nu_b) {
     return (wet_a && wet_b) ? tmax(nu_a, nu_b) : T(0);
 }
 
-// S15 for one field of a cell: out + kappa * (x term + y term) with the
-// level-n values c (cell), l/r (x neighbours), b/t (y neighbours).
+// S15 dissipation flux through one face: eps * (phi_above - phi_below).
 template <class T>
-__device__ __forceinline__ T dissip(T out, T c, T l, T r, T b, T t, T ee, T ew, T en, T es, T kappa) {
-    T tx = fma_(ee, r - c, -(ew * (c - l)));
-    T ty = fma_(en, t - c, -(es * (c - b)));
-    return fma_(kappa, tx + ty, out);
+__device__ __forceinline__ T dflux(T eps, T hi, T lo) { return eps * (hi - lo); }
+
+// S15 for one field of a cell from its four face fluxes (east, west, north,
+// south): out + kappa * ((fe - fw) + (fn - fs)).  Every kernel form builds the
+// same face fluxes with dflux, so a face is rounded the same from both sides.
+template <class T>
+__device__ __forceinline__ T dissip_faces(T out, T fe, T fw, T fn, T fs, T kappa) {
+    return fma_(kappa, (fe - fw) + (fn - fs), out);
 }
 
 // CFL speed of a cell (S2); 0 for dry cells.

@@ -42,7 +42,7 @@ namespace swe {
 namespace fz {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int NWARP = 4;           // warps per CTA
+constexpr int NWARP = 1;           // warps per CTA (one: item and row branches are then CTA-uniform)
 constexpr int NSLOT = 8;           // ring slots per warp (a power of two)
 constexpr int NPRE = NSLOT - 4;    // rows loaded ahead of the current row
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // cycles (~2 s) before a wait gives up
@@ -56,6 +56,7 @@ struct Geo {
     static constexpr int FSTRIDE = ((BW * (int)sizeof(T) + 127) / 128) * 128;  // bytes per field row
     static constexpr int SLOT = 4 * FSTRIDE;              // bytes per ring slot (eta, u, v, z)
     static constexpr int WARP_SMEM = NSLOT * SLOT;
+    static constexpr int MINB = (sizeof(T) == 4 && CPT <= 2) ? 16 : 8;  // CTAs per SM the registers must allow
 };
 
 template <class T>
@@ -138,9 +139,41 @@ template <class T, int CPT>
 struct Row {  // eta, u, v, z of the lane's CPT cells in one row
     T e[CPT], u[CPT], v[CPT], z[CPT];
 };
+
 template <class T, int CPT>
-struct PRow {  // predicted eta, u, v
-    T e[CPT], u[CPT], v[CPT];
+struct PR {  // a predicted row as the corrector needs it: eta*, u*, v*, bed, h* v*
+    T e[CPT], u[CPT], v[CPT], z[CPT], qy[CPT];
+};
+
+// State carried from one row to the next, double-buffered by row parity so
+// that unrolling the row loop by two needs no register copies: the values of
+// the row just produced go to index PAR, the previous row's are at 1 - PAR.
+template <class T, int CPT>
+struct Carry {
+    PR<T, CPT> P[2];      // predicted rows
+    T NY[2][CPT];         // y dissipation switch of a level-n row
+    T FY[2][3][CPT];      // y dissipation face flux (eta, u, v) above a row
+    T DX[2][3][CPT];      // x dissipation (east minus west face flux) of a row
+};
+
+struct Acc {  // per-warp totals over its items, FP64
+    double clamp, bw, be, bs, bn, smax;
+    bool bad;
+};
+
+template <class T>
+struct ItemAcc {  // per-item totals in the state's real type
+    T clamp, bw, be, bs, bn, smax;
+    bool bad;
+};
+
+template <class T, int CPT>
+struct ItemCtx {
+    unsigned char* ring;
+    uint64_t* bars;
+    int lane, xw, xb, col, x0c, y0, y1, nr;
+    bool out_lane, edge;
+    unsigned g0;
 };
 
 template <class T, int CPT>
@@ -170,412 +203,451 @@ __device__ __forceinline__ T shdn(T x) { return __shfl_down_sync(FULL, x, 1); }
 template <class T>
 __device__ __forceinline__ T shup(T x) { return __shfl_up_sync(FULL, x, 1); }
 
-// Neighbours of the lane's cells one column to the right (D > 0) or left
-// (D < 0): the next cell of the lane, else the adjacent lane's end cell;
-// the strip-edge lane takes the ring's halo column value h.
+// Values one column to the right (D > 0) or left (D < 0) of the lane's
+// cells: the lane's next cell, else the adjacent lane's end cell; the
+// strip-edge lane on that side takes `halo` when `use_halo`.
 template <int D, class T, int CPT>
-__device__ __forceinline__ void shift(const T (&a)[CPT], T halo, bool edge_lane, T (&o)[CPT]) {
+__device__ __forceinline__ void shift(const T (&a)[CPT], T halo, bool use_halo, T (&o)[CPT]) {
     if (D > 0) {
 #pragma unroll
         for (int c = 0; c + 1 < CPT; ++c) o[c] = a[c + 1];
-        T t = shdn(a[0]);
-        o[CPT - 1] = edge_lane ? halo : t;
+        const T t = shdn(a[0]);
+        o[CPT - 1] = use_halo ? halo : t;
     } else {
 #pragma unroll
         for (int c = 1; c < CPT; ++c) o[c] = a[c - 1];
-        T t = shup(a[CPT - 1]);
-        o[0] = edge_lane ? halo : t;
+        const T t = shup(a[CPT - 1]);
+        o[0] = use_halo ? halo : t;
     }
 }
 
-// x neighbours of a level-n row on side D; the halo is read on that side only.
-template <int D, class T, int CPT>
-__device__ __forceinline__ void row_shift(const Row<T, CPT>& r, const unsigned char* slot, int col, int lane,
-                                          Row<T, CPT>& o) {
-    const int hc = D > 0 ? col + CPT : col - 1;
-    const bool el = D > 0 ? lane == 31 : lane == 0;
-    shift<D, T, CPT>(r.e, ld1<T, CPT>(slot, 0, hc), el, o.e);
-    shift<D, T, CPT>(r.u, ld1<T, CPT>(slot, 1, hc), el, o.u);
-    shift<D, T, CPT>(r.v, ld1<T, CPT>(slot, 2, hc), el, o.v);
-    shift<D, T, CPT>(r.z, ld1<T, CPT>(slot, 3, hc), el, o.z);
-}
-// x neighbours without a halo (the lane that would need it never outputs).
-template <int D, class T, int CPT>
-__device__ __forceinline__ void row_shift_nohalo(const Row<T, CPT>& r, Row<T, CPT>& o) {
-    shift<D, T, CPT>(r.e, T(0), false, o.e);
-    shift<D, T, CPT>(r.u, T(0), false, o.u);
-    shift<D, T, CPT>(r.v, T(0), false, o.v);
-    shift<D, T, CPT>(r.z, T(0), false, o.z);
-}
-
-struct Acc {
-    double clamp, bw, be, bs, bn;
-    double smax;
-    bool bad;
-};
-
-// Process one work item: rows [y0, y1) of the strip whose window starts at xw.
-// One loop iteration per ring row r: y switch and predictor of row r-1,
-// corrector/average/dissipation/fix of row r-2.
-template <class T, int CPT, int SX, int SY, bool KAPPA>
-__device__ __forceinline__ void run_item(const Args<T>& A, const StepK<T>& S, Acc& acc, unsigned char* ring,
-                                         uint64_t* bars, int lane, int xw, int y0, int y1, unsigned& g0,
-                                         const CUtensorMap* tme, const CUtensorMap* tmu, const CUtensorMap* tmv,
-                                         const CUtensorMap* tmz, bool& timed_out) {
+// Predicated issue of one ring row: lane 0 arms the barrier and starts the
+// four tile loads (no divergent branch).
+template <class T, int CPT>
+__device__ __forceinline__ void issue_row(const ItemCtx<T, CPT>& I, int k, const CUtensorMap* tme,
+                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz) {
     using Gm = Geo<T, CPT>;
+    const unsigned g = I.g0 + (unsigned)k;
+    const unsigned bar = saddr(I.bars + (g & (NSLOT - 1)));
+    const unsigned dst = saddr(I.ring + (g & (NSLOT - 1)) * Gm::SLOT);
+    const unsigned pred = I.lane == 0 ? 1u : 0u;
+    const int y = I.y0 - 2 + k;
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}"
+                 ::"r"(pred), "r"(bar), "r"(4u * Gm::BW * (unsigned)sizeof(T)) : "memory");
+    const CUtensorMap* maps[4] = {tme, tmu, tmv, tmz};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n"
+            " @p cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%1], [%2, {%3, %4}], [%5];\n}"
+            ::"r"(pred), "r"(dst + f * Gm::FSTRIDE), "l"(maps[f]), "r"(I.xb), "r"(y), "r"(bar) : "memory");
+}
+
+// Waits for ring row k; false (for the whole warp) when the wait gave up.
+template <class T, int CPT>
+__device__ __forceinline__ bool wait_row(const ItemCtx<T, CPT>& I, int k) {
+    const unsigned g = I.g0 + (unsigned)k;
+    uint64_t* bar = I.bars + (g & (NSLOT - 1));
+    const unsigned par = (g / NSLOT) & 1u;
+    if (__all_sync(FULL, mbar_try(bar, par))) return true;
+    const unsigned long long t0 = clock64();
+    while (!__all_sync(FULL, mbar_try(bar, par)))
+        if (clock64() - t0 > WAIT_LIMIT) return false;
+    return true;
+}
+
+template <class T, int CPT>
+__device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CPT>& I, int row, int ny) {
+    const int src = row < 0 ? 0 : (row >= ny ? ny - 1 : row);
+    return I.ring + ((I.g0 + (unsigned)(src - (I.y0 - 2))) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+}
+
+// One ring row r (ring index k) of an item: y switch of row r-1, the
+// predictor and x dissipation of row r-1, and the corrector, average,
+// dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.
+template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR>
+__device__ __forceinline__ void row_step(const Args<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
+                                         Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
+                                         const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
+                                         bool& timed_out) {
     constexpr int CX = -SX, CY = -SY;
+    constexpr int Q = PAR, O = 1 - PAR;  // this row's buffers, the previous row's
     const GridK<T>& G = A.G;
     const int ny = G.ny, nx = G.nx;
     const T hd = G.h_dry;
-    const int xb = (xw - 2) & ~(Gm::ALIGN - 1);  // TMA box start, 16-byte aligned
-    const int col = (xw - xb) + CPT * lane;      // ring column of the lane's first cell
-    const int x0c = xw + CPT * lane;             // grid column of the lane's first cell
-    const int nr = y1 - y0 + 4;
-    const bool out_lane = SX > 0 ? lane != 0 : lane != 31;
-    const bool edge = (xw - 2 < 0) || (xw + Gm::W + 1 > nx - 1);  // strip touches the x boundary
-    constexpr unsigned BYTES = 4u * Gm::BW * sizeof(T);
+    const int lane = I.lane;
+    const int r = I.y0 - 2 + k;
 
-    auto issue = [&](int k) {
-        if (lane == 0 && k < nr) {
-            const unsigned g = g0 + (unsigned)k;
-            uint64_t* bar = bars + (g & (NSLOT - 1));
-            unsigned char* dst = ring + (g & (NSLOT - 1)) * Gm::SLOT;
-            const int y = y0 - 2 + k;
-            mbar_expect(bar, BYTES);
-            tma_row(dst + 0 * Gm::FSTRIDE, tme, bar, xb, y);
-            tma_row(dst + 1 * Gm::FSTRIDE, tmu, bar, xb, y);
-            tma_row(dst + 2 * Gm::FSTRIDE, tmv, bar, xb, y);
-            tma_row(dst + 3 * Gm::FSTRIDE, tmz, bar, xb, y);
-        }
-    };
-    fence_async_smem();  // the previous item's rows were read through the generic proxy
-#pragma unroll
-    for (int k = 0; k < NPRE; ++k) issue(k);
+    fence_async_smem();  // ring row k-4 (read last iteration) is refilled next
+    if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
+    if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
+    if (k < 2) return;
 
-    auto slot_of = [&](int row) -> const unsigned char* {  // clamped to the grid
-        const int src = row < 0 ? 0 : (row >= ny ? ny - 1 : row);
-        return ring + ((g0 + (unsigned)(src - (y0 - 2))) & (NSLOT - 1)) * Gm::SLOT;
-    };
-
-    PRow<T, CPT> PA, PB;   // predicted rows C-1 and C
-    T NA[CPT], NB[CPT];    // y switches of rows C-1 and C
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-        NA[j] = NB[j] = T(0);
-        PA.e[j] = PA.u[j] = PA.v[j] = PB.e[j] = PB.u[j] = PB.v[j] = T(0);
+    // -------- level-n rows r, r-1, r-2 (ghost cells outside [0, ny))
+    const bool brow = (r - 2 <= 0) || (r >= ny);
+    const unsigned g = I.g0 + (unsigned)k;
+    const unsigned char* s0 = I.ring + ((g) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+    const unsigned char* s1 = I.ring + ((g - 1u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+    const unsigned char* s2 = I.ring + ((g - 2u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+    if (brow) {
+        s0 = slot_clamped(I, r, ny);
+        s1 = slot_clamped(I, r - 1, ny);
+        s2 = slot_clamped(I, r - 2, ny);
     }
-    T clamp_i = T(0), bw_i = T(0), be_i = T(0), bs_i = T(0), bn_i = T(0), smax_i = T(0);
-    bool bad_i = false;
-    int waited = 0;
-
-#pragma unroll 1
-    for (int k = 0; k < nr; ++k) {
-        const int r = y0 - 2 + k;
-        fence_async_smem();
-        issue(k + NPRE);  // into the slot of ring row k-4, consumed last iteration
-        {
-            const unsigned g = g0 + (unsigned)k;
-            const bool ok = mbar_wait(bars + (g & (NSLOT - 1)), (g / NSLOT) & 1u);
-            if (__any_sync(FULL, !ok)) { timed_out = true; break; }
-            waited = k + 1;
-        }
-        if (k < 2) { __syncwarp(); continue; }
-        // rows r (0), r-1 (1), r-2 (2), r-3 (3); ghosted outside [0, ny)
-        const bool brow = (r - 3 < 0) || (r >= ny);
-        const unsigned char* s0 = slot_of(r);
-        const unsigned char* s1 = slot_of(r - 1);
-        const unsigned char* s2 = slot_of(r - 2);
-        const unsigned char* s3 = slot_of(r - 3);
-        Row<T, CPT> R0, R1, R2, R3;
-        ld_row<T, CPT>(s0, col, R0);
-        ld_row<T, CPT>(s1, col, R1);
-        ld_row<T, CPT>(s2, col, R2);
-        if (KAPPA || k >= 4) ld_row<T, CPT>(s3, col, R3);
-        if (brow) {
-            if (r < 0) ghost_row(R0, SIDE_S, G); else if (r >= ny) ghost_row(R0, SIDE_N, G);
-            if (r - 1 < 0) ghost_row(R1, SIDE_S, G); else if (r - 1 >= ny) ghost_row(R1, SIDE_N, G);
-            if (r - 2 < 0) ghost_row(R2, SIDE_S, G); else if (r - 2 >= ny) ghost_row(R2, SIDE_N, G);
-            if (r - 3 < 0) ghost_row(R3, SIDE_S, G); else if (r - 3 >= ny) ghost_row(R3, SIDE_N, G);
-        }
-        // ---------------- y switch of row r-1 (S15 input)
-        T NN[CPT];
-        if (KAPPA) {
+    Row<T, CPT> R0, R1, R2;
+    ld_row<T, CPT>(s0, I.col, R0);
+    ld_row<T, CPT>(s1, I.col, R1);
+    ld_row<T, CPT>(s2, I.col, R2);
+    if (brow) {
+        if (r < 0) ghost_row(R0, SIDE_S, G); else if (r >= ny) ghost_row(R0, SIDE_N, G);
+        if (r - 1 < 0) ghost_row(R1, SIDE_S, G); else if (r - 1 >= ny) ghost_row(R1, SIDE_N, G);
+        if (r - 2 < 0) ghost_row(R2, SIDE_S, G); else if (r - 2 >= ny) ghost_row(R2, SIDE_N, G);
+    }
+    T h0[CPT], h1[CPT], h2[CPT];
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) NN[j] = nu_switch(R2.e[j] - R2.z[j], R1.e[j] - R1.z[j], R0.e[j] - R0.z[j]);
+    for (int j = 0; j < CPT; ++j) { h0[j] = R0.e[j] - R0.z[j]; h1[j] = R1.e[j] - R1.z[j]; h2[j] = R2.e[j] - R2.z[j]; }
+
+    // -------- y switch of row r-1, y dissipation flux through the face between rows r-2 and r-1
+    if (KAPPA) {
+        const bool face_in = !brow || (r - 2 >= 0 && r - 1 < ny);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const T nyn = nu_switch(h2[j], h1[j], h0[j]);
+            T eps = face_eps(h2[j] > hd, h1[j] > hd, Cy.NY[O][j], nyn);
+            eps = face_in ? eps : T(0);
+            Cy.FY[Q][0][j] = dflux(eps, R1.e[j], R2.e[j]);
+            Cy.FY[Q][1][j] = dflux(eps, R1.u[j], R2.u[j]);
+            Cy.FY[Q][2][j] = dflux(eps, R1.v[j], R2.v[j]);
+            Cy.NY[Q][j] = nyn;
         }
-        // ---------------- predictor of row p = r-1 (S1-S8)
-        PRow<T, CPT> PN;
+    }
+
+    // -------- predictor and x dissipation of row p = r-1
+    auto predictor = [&]() {
         const int p = r - 1;
-        {
-            const Row<T, CPT>& c = R1;
-            const Row<T, CPT>& yn = SY > 0 ? R0 : R2;
-            Row<T, CPT> xn;
-            row_shift<SX, T, CPT>(c, s1, col, lane, xn);
-            T hc[CPT], qxc[CPT], qyc[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
+        const Row<T, CPT>& c = R1;
+        const Row<T, CPT>& yn = SY > 0 ? R0 : R2;
+        const T* hyn = SY > 0 ? h0 : h2;
+        // x neighbours: on the predictor's side with the ring halo (that edge lane outputs)
+        const int hcol = SX > 0 ? I.col + CPT : I.col - 1;
+        const bool edge_lane = SX > 0 ? lane == 31 : lane == 0;
+        Row<T, CPT> xn;
+        shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), edge_lane, xn.e);
+        shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), edge_lane, xn.u);
+        shift<SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, hcol), edge_lane, xn.v);
+        shift<SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, hcol), edge_lane, xn.z);
+        if (brow && (r - 1 < 0 || r - 1 >= ny)) {  // halo column of a ghost row
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                if (edge_lane && (SX > 0 ? j == CPT - 1 : j == 0)) {
+                    Cell<T> q; q.e = xn.e[j]; q.u = xn.u[j]; q.v = xn.v[j]; q.z = xn.z[j];
+                    q = ghost(q, r - 1 < 0 ? SIDE_S : SIDE_N, G);
+                    xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
+                }
+        }
+        T qx[CPT], qy[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            qx[j] = h1[j] * c.u[j];
+            qy[j] = h1[j] * c.v[j];
+            const T qxn = (xn.e[j] - xn.z[j]) * xn.u[j];
+            const T qyn = hyn[j] * yn.v[j];
+            if (SX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
+            if (SY > 0) { fn[j] = qyn; fs[j] = qy[j]; } else { fn[j] = qy[j]; fs[j] = qyn; }
+        }
+        if (I.edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                hc[j] = c.e[j] - c.z[j];
-                qxc[j] = hc[j] * c.u[j];
-                qyc[j] = hc[j] * c.v[j];
-                const T qxn = (xn.e[j] - xn.z[j]) * xn.u[j];
-                const T qyn = (yn.e[j] - yn.z[j]) * yn.v[j];
-                if (SX > 0) { fe[j] = qxn; fw[j] = qxc[j]; } else { fe[j] = qxc[j]; fw[j] = qxn; }
-                if (SY > 0) { fn[j] = qyn; fs[j] = qyc[j]; } else { fn[j] = qyc[j]; fs[j] = qyn; }
-            }
-            if (edge) {
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    const int x = x0c + j;
-                    if (x == 0) fw[j] = face_bnd(SIDE_W, qxc[j], G);
-                    if (x == nx - 1) fe[j] = face_bnd(SIDE_E, qxc[j], G);
-                    if (SX > 0 ? x == nx - 1 : x == 0) {
-                        Cell<T> q; q.e = c.e[j]; q.u = c.u[j]; q.v = c.v[j]; q.z = c.z[j];
-                        q = ghost(q, SX > 0 ? SIDE_E : SIDE_W, G);
-                        xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
-                    }
+                const int x = I.x0c + j;
+                if (x == 0) fw[j] = face_bnd(SIDE_W, qx[j], G);
+                if (x == nx - 1) fe[j] = face_bnd(SIDE_E, qx[j], G);
+                if (SX > 0 ? x == nx - 1 : x == 0) {
+                    Cell<T> q; q.e = c.e[j]; q.u = c.u[j]; q.v = c.v[j]; q.z = c.z[j];
+                    q = ghost(q, SX > 0 ? SIDE_E : SIDE_W, G);
+                    xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
                 }
             }
+        }
+        if (brow) {
             if (p == 0) {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) fs[j] = face_bnd(SIDE_S, qyc[j], G);
+                for (int j = 0; j < CPT; ++j) fs[j] = face_bnd(SIDE_S, qy[j], G);
             }
             if (p == ny - 1) {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, qyc[j], G);
+                for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, qy[j], G);
             }
-            T gn2v[CPT];
-            if (A.n2 != nullptr) {
-                int xc = x0c < 0 ? 0 : (x0c > G.pitch - CPT ? G.pitch - CPT : x0c);
-                const int pr = p < 0 ? 0 : (p >= ny ? ny - 1 : p);
-                ld_vec<T, CPT>(A.n2 + (size_t)pr * G.pitch + xc, gn2v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
-            }
-            T added = T(0);
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                Cell<T> cc, cx, cy;
-                cc.e = c.e[j]; cc.u = c.u[j]; cc.v = c.v[j]; cc.z = c.z[j];
-                cx.e = xn.e[j]; cx.u = xn.u[j]; cx.v = xn.v[j]; cx.z = xn.z[j];
-                cy.e = yn.e[j]; cy.u = yn.u[j]; cy.v = yn.v[j]; cy.z = yn.z[j];
-                T eo, uo, vo;
-                stage<SX, SY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], cc.e, cc.u, cc.v, gn2v[j], S, hd, eo, uo, vo);
-                T ad = wetdry_fix(eo, uo, vo, cc.z, hd);
-                if (edge && x0c + j >= nx) ad = T(0);
-                added += ad;
-                PN.e[j] = eo; PN.u[j] = uo; PN.v[j] = vo;
-            }
-            // a predicted clamp counts once per cell: in the item and lane that output it
-            // (a lane's CPT cells never straddle column 0)
-            const bool own = out_lane && p >= y0 && p < y1 && x0c >= 0;
-            if (own) clamp_i = fma_(T(0.5), added, clamp_i);
         }
-        // ---------------- corrector/average/dissipation/fix of row C = r-2 (S9-S16)
-        const int C = r - 2;
-        if (k >= 4) {
-            const Row<T, CPT>& n0 = R2;
-            Row<T, CPT> cs, ys, xs;
+        T gn2v[CPT];
+        if (A.n2 != nullptr) {
+            const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
+            const int pr = p < 0 ? 0 : (p >= ny ? ny - 1 : p);
+            ld_vec<T, CPT>(A.n2 + (size_t)pr * G.pitch + xc, gn2v);
+        } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                cs.e[j] = PB.e[j]; cs.u[j] = PB.u[j]; cs.v[j] = PB.v[j]; cs.z[j] = n0.z[j];
-                if (CY < 0) { ys.e[j] = PA.e[j]; ys.u[j] = PA.u[j]; ys.v[j] = PA.v[j]; ys.z[j] = R3.z[j]; }
-                else        { ys.e[j] = PN.e[j]; ys.u[j] = PN.u[j]; ys.v[j] = PN.v[j]; ys.z[j] = R1.z[j]; }
-            }
-            if (CY < 0 ? C == 0 : C == ny - 1) { ys = cs; ghost_row(ys, CY < 0 ? SIDE_S : SIDE_N, G); }
-            row_shift_nohalo<CX, T, CPT>(cs, xs);  // the lane that would need a halo never outputs
-            T qxs[CPT], qys[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
+            for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
+        }
+        PR<T, CPT>& P = Cy.P[Q];
+        T added = T(0);
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                const T h = cs.e[j] - cs.z[j];
-                qxs[j] = h * cs.u[j];
-                qys[j] = h * cs.v[j];
-                const T qxn = (xs.e[j] - xs.z[j]) * xs.u[j];
-                const T qyn = (ys.e[j] - ys.z[j]) * ys.v[j];
-                if (CX > 0) { fe[j] = qxn; fw[j] = qxs[j]; } else { fe[j] = qxs[j]; fw[j] = qxn; }
-                if (CY > 0) { fn[j] = qyn; fs[j] = qys[j]; } else { fn[j] = qys[j]; fs[j] = qyn; }
-            }
-            if (edge) {
+        for (int j = 0; j < CPT; ++j) {
+            Cell<T> cc, cx, cy;
+            cc.e = c.e[j]; cc.u = c.u[j]; cc.v = c.v[j]; cc.z = c.z[j];
+            cx.e = xn.e[j]; cx.u = xn.u[j]; cx.v = xn.v[j]; cx.z = xn.z[j];
+            cy.e = yn.e[j]; cy.u = yn.u[j]; cy.v = yn.v[j]; cy.z = yn.z[j];
+            T eo, uo, vo;
+            stage<SX, SY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], cc.e, cc.u, cc.v, gn2v[j], S, hd, eo, uo, vo);
+            T ad = wetdry_fix(eo, uo, vo, cc.z, hd);
+            if (I.edge && I.x0c + j >= nx) ad = T(0);
+            added += ad;
+            P.e[j] = eo; P.u[j] = uo; P.v[j] = vo; P.z[j] = cc.z;
+            P.qy[j] = (eo - cc.z) * vo;
+        }
+        // a predicted clamp counts once per cell: in the item and lane that output it
+        if (I.out_lane && p >= I.y0 && p < I.y1 && I.x0c >= 0) ia.clamp = fma_(T(0.5), added, ia.clamp);
+
+        if (KAPPA) {
+            // x dissipation of row r-1: the other side's neighbours need no halo
+            // (the lane at that strip edge never outputs)
+            Row<T, CPT> xo;
+            shift<-SX, T, CPT>(c.e, T(0), false, xo.e);
+            shift<-SX, T, CPT>(c.u, T(0), false, xo.u);
+            shift<-SX, T, CPT>(c.v, T(0), false, xo.v);
+            shift<-SX, T, CPT>(c.z, T(0), false, xo.z);
+            const Row<T, CPT>& L = SX > 0 ? xo : xn;  // left neighbours
+            const Row<T, CPT>& Rr = SX > 0 ? xn : xo; // right neighbours
+            T hl[CPT], hr[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) { hl[j] = L.e[j] - L.z[j]; hr[j] = Rr.e[j] - Rr.z[j]; }
+            if (I.edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
-                    const int x = x0c + j;
-                    if (x == 0) fw[j] = face_bnd(SIDE_W, qxs[j], G);
-                    if (x == nx - 1) fe[j] = face_bnd(SIDE_E, qxs[j], G);
-                    if (CX > 0 ? x == nx - 1 : x == 0) {
-                        Cell<T> q; q.e = cs.e[j]; q.u = cs.u[j]; q.v = cs.v[j]; q.z = cs.z[j];
-                        q = ghost(q, CX > 0 ? SIDE_E : SIDE_W, G);
-                        xs.e[j] = q.e; xs.u[j] = q.u; xs.v[j] = q.v; xs.z[j] = q.z;
-                    }
+                    if (I.x0c + j == 0) hl[j] = h1[j];
+                    if (I.x0c + j == nx - 1) hr[j] = h1[j];
                 }
             }
+            T nuc[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) nuc[j] = nu_switch(hl[j], h1[j], hr[j]);
+            // switch one column outside the lane: adjacent lane, or from the ring at the output edge
+            T nu_lo = shup(nuc[CPT - 1]), nu_hi = shdn(nuc[0]);
+            if (SX > 0) {
+                const T h2x = ld1<T, CPT>(s1, 0, I.col + CPT + 1) - ld1<T, CPT>(s1, 3, I.col + CPT + 1);
+                const T ext = nu_switch(h1[CPT - 1], hr[CPT - 1], h2x);
+                nu_hi = lane == 31 ? ext : nu_hi;
+            } else {
+                const T h2x = ld1<T, CPT>(s1, 0, I.col - 2) - ld1<T, CPT>(s1, 3, I.col - 2);
+                const T ext = nu_switch(h2x, hl[0], h1[0]);
+                nu_lo = lane == 0 ? ext : nu_lo;
+            }
+            // east face of every cell, west face of the first
+            T fr[3][CPT], fl0[3];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const T nur = j + 1 < CPT ? nuc[j + 1 < CPT ? j + 1 : j] : nu_hi;
+                T eps = face_eps(h1[j] > hd, hr[j] > hd, nuc[j], nur);
+                if (I.edge && I.x0c + j + 1 >= nx) eps = T(0);
+                fr[0][j] = dflux(eps, Rr.e[j], c.e[j]);
+                fr[1][j] = dflux(eps, Rr.u[j], c.u[j]);
+                fr[2][j] = dflux(eps, Rr.v[j], c.v[j]);
+            }
+            {
+                T eps = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
+                if (I.edge && I.x0c - 1 < 0) eps = T(0);
+                fl0[0] = dflux(eps, c.e[0], L.e[0]);
+                fl0[1] = dflux(eps, c.u[0], L.u[0]);
+                fl0[2] = dflux(eps, c.v[0], L.v[0]);
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) Cy.DX[Q][f][j] = fr[f][j] - (j == 0 ? fl0[f] : fr[f][j > 0 ? j - 1 : 0]);
+        }
+    };
+
+    // -------- corrector, average, dissipation and fix of row C = r-2
+    auto corrector = [&]() {
+        const int C = r - 2;
+        const PR<T, CPT>& pc = Cy.P[O];       // predicted row C
+        PR<T, CPT> ys = Cy.P[Q];              // row C-1 (forward predictor) or C+1 (backward)
+        Row<T, CPT> cs;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) { cs.e[j] = pc.e[j]; cs.u[j] = pc.u[j]; cs.v[j] = pc.v[j]; cs.z[j] = pc.z[j]; }
+        if (brow && (CY < 0 ? C == 0 : C == ny - 1)) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                Cell<T> q; q.e = cs.e[j]; q.u = cs.u[j]; q.v = cs.v[j]; q.z = cs.z[j];
+                q = ghost(q, CY < 0 ? SIDE_S : SIDE_N, G);
+                ys.e[j] = q.e; ys.u[j] = q.u; ys.v[j] = q.v; ys.z[j] = q.z;
+                ys.qy[j] = (q.e - q.z) * q.v;
+            }
+        }
+        Row<T, CPT> xs;  // the lane that would need a halo on this side never outputs
+        shift<CX, T, CPT>(cs.e, T(0), false, xs.e);
+        shift<CX, T, CPT>(cs.u, T(0), false, xs.u);
+        shift<CX, T, CPT>(cs.v, T(0), false, xs.v);
+        shift<CX, T, CPT>(cs.z, T(0), false, xs.z);
+        T qx[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            qx[j] = (cs.e[j] - cs.z[j]) * cs.u[j];
+            const T qxn = (xs.e[j] - xs.z[j]) * xs.u[j];
+            if (CX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
+            if (CY > 0) { fn[j] = ys.qy[j]; fs[j] = pc.qy[j]; } else { fn[j] = pc.qy[j]; fs[j] = ys.qy[j]; }
+        }
+        if (I.edge) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const int x = I.x0c + j;
+                if (x == 0) fw[j] = face_bnd(SIDE_W, qx[j], G);
+                if (x == nx - 1) fe[j] = face_bnd(SIDE_E, qx[j], G);
+                if (CX > 0 ? x == nx - 1 : x == 0) {
+                    Cell<T> q; q.e = cs.e[j]; q.u = cs.u[j]; q.v = cs.v[j]; q.z = cs.z[j];
+                    q = ghost(q, CX > 0 ? SIDE_E : SIDE_W, G);
+                    xs.e[j] = q.e; xs.u[j] = q.u; xs.v[j] = q.v; xs.z[j] = q.z;
+                }
+            }
+        }
+        if (brow) {
             if (C == 0) {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) fs[j] = face_bnd(SIDE_S, qys[j], G);
+                for (int j = 0; j < CPT; ++j) fs[j] = face_bnd(SIDE_S, pc.qy[j], G);
             }
             if (C == ny - 1) {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, qys[j], G);
+                for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, pc.qy[j], G);
             }
-            T gn2v[CPT];
-            if (A.n2 != nullptr) {
-                int xc = x0c < 0 ? 0 : (x0c > G.pitch - CPT ? G.pitch - CPT : x0c);
-                ld_vec<T, CPT>(A.n2 + (size_t)C * G.pitch + xc, gn2v);
-            } else {
+        }
+        T gn2v[CPT];
+        if (A.n2 != nullptr) {
+            const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
+            ld_vec<T, CPT>(A.n2 + (size_t)C * G.pitch + xc, gn2v);
+        } else {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
-            }
-            T oe[CPT], ou[CPT], ov[CPT];
+            for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
+        }
+        T oe[CPT], ou[CPT], ov[CPT];
+        T added = T(0), sp = T(0);
+        bool bad = false;
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                Cell<T> cc, cx, cy;
-                cc.e = cs.e[j]; cc.u = cs.u[j]; cc.v = cs.v[j]; cc.z = cs.z[j];
-                cx.e = xs.e[j]; cx.u = xs.u[j]; cx.v = xs.v[j]; cx.z = xs.z[j];
-                cy.e = ys.e[j]; cy.u = ys.u[j]; cy.v = ys.v[j]; cy.z = ys.z[j];
-                T eo, uo, vo;
-                stage<CX, CY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], n0.e[j], n0.u[j], n0.v[j], gn2v[j], S, hd, eo,
-                              uo, vo);
-                oe[j] = T(0.5) * (cc.e + eo);
-                ou[j] = T(0.5) * (cc.u + uo);
-                ov[j] = T(0.5) * (cc.v + vo);
-            }
+        for (int j = 0; j < CPT; ++j) {
+            Cell<T> cc, cx, cy;
+            cc.e = cs.e[j]; cc.u = cs.u[j]; cc.v = cs.v[j]; cc.z = cs.z[j];
+            cx.e = xs.e[j]; cx.u = xs.u[j]; cx.v = xs.v[j]; cx.z = xs.z[j];
+            cy.e = ys.e[j]; cy.u = ys.u[j]; cy.v = ys.v[j]; cy.z = ys.z[j];
+            T eo, uo, vo;
+            stage<CX, CY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], R2.e[j], R2.u[j], R2.v[j], gn2v[j], S, hd, eo, uo,
+                          vo);
+            oe[j] = T(0.5) * (cc.e + eo);
+            ou[j] = T(0.5) * (cc.u + uo);
+            ov[j] = T(0.5) * (cc.v + vo);
             if (KAPPA) {
-                // level-n neighbours of row C; the halo is needed on the output side only
-                Row<T, CPT> nl, nr;
-                if (SX > 0) {
-                    row_shift_nohalo<-1, T, CPT>(n0, nl);
-                    row_shift<+1, T, CPT>(n0, s2, col, lane, nr);
-                } else {
-                    row_shift<-1, T, CPT>(n0, s2, col, lane, nl);
-                    row_shift_nohalo<+1, T, CPT>(n0, nr);
-                }
-                T h0[CPT], hl[CPT], hr[CPT];
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    h0[j] = n0.e[j] - n0.z[j];
-                    hl[j] = nl.e[j] - nl.z[j];
-                    hr[j] = nr.e[j] - nr.z[j];
-                }
-                if (edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
-                        if (x0c + j == 0) hl[j] = h0[j];
-                        if (x0c + j == nx - 1) hr[j] = h0[j];
-                    }
-                }
-                T nuc[CPT], nul[CPT], nur[CPT];
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) nuc[j] = nu_switch(hl[j], h0[j], hr[j]);
-                {
-                    // switch one column outside the lane: from the adjacent lane, or
-                    // computed from the ring on the output side of the strip edge
-                    T lo = shup(nuc[CPT - 1]), hi = shdn(nuc[0]);
-                    if (SX > 0) {
-                        const T h2 = ld1<T, CPT>(s2, 0, col + CPT + 1) - ld1<T, CPT>(s2, 3, col + CPT + 1);
-                        const T ext = nu_switch(h0[CPT - 1], hr[CPT - 1], h2);
-                        hi = lane == 31 ? ext : hi;
-                    } else {
-                        const T h2 = ld1<T, CPT>(s2, 0, col - 2) - ld1<T, CPT>(s2, 3, col - 2);
-                        const T ext = nu_switch(h2, hl[0], h0[0]);
-                        lo = lane == 0 ? ext : lo;
-                    }
-#pragma unroll
-                    for (int j = 1; j < CPT; ++j) nul[j] = nuc[j - 1];
-#pragma unroll
-                    for (int j = 0; j + 1 < CPT; ++j) nur[j] = nuc[j + 1];
-                    nul[0] = lo;
-                    nur[CPT - 1] = hi;
-                }
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    const bool wc = h0[j] > hd;
-                    T ee = face_eps(wc, hr[j] > hd, nuc[j], nur[j]);
-                    T ew = face_eps(hl[j] > hd, wc, nul[j], nuc[j]);
-                    T en = face_eps(wc, (R1.e[j] - R1.z[j]) > hd, NB[j], NN[j]);
-                    T es = face_eps((R3.e[j] - R3.z[j]) > hd, wc, NA[j], NB[j]);
-                    if (edge) {
-                        if (x0c + j + 1 >= nx) ee = T(0);
-                        if (x0c + j - 1 < 0) ew = T(0);
-                    }
-                    if (C + 1 >= ny) en = T(0);
-                    if (C - 1 < 0) es = T(0);
-                    oe[j] = dissip(oe[j], n0.e[j], nl.e[j], nr.e[j], R3.e[j], R1.e[j], ee, ew, en, es, G.kappa);
-                    ou[j] = dissip(ou[j], n0.u[j], nl.u[j], nr.u[j], R3.u[j], R1.u[j], ee, ew, en, es, G.kappa);
-                    ov[j] = dissip(ov[j], n0.v[j], nl.v[j], nr.v[j], R3.v[j], R1.v[j], ee, ew, en, es, G.kappa);
-                }
+                // the x face fluxes come as their difference (east minus west); the
+                // y ones are this row's north face and the previous row's
+                oe[j] = fma_(G.kappa, Cy.DX[O][0][j] + (Cy.FY[Q][0][j] - Cy.FY[O][0][j]), oe[j]);
+                ou[j] = fma_(G.kappa, Cy.DX[O][1][j] + (Cy.FY[Q][1][j] - Cy.FY[O][1][j]), ou[j]);
+                ov[j] = fma_(G.kappa, Cy.DX[O][2][j] + (Cy.FY[Q][2][j] - Cy.FY[O][2][j]), ov[j]);
             }
-            // S16: fix, the next step's CFL speed, tallies, store
-            T added = T(0), sp = T(0);
-            bool badc = false;
+            T ad = wetdry_fix(oe[j], ou[j], ov[j], cc.z, hd);
+            T spj = cfl_speed(oe[j], ou[j], ov[j], cc.z, G);
+            const T sum = oe[j] + ou[j] + ov[j];
+            const bool bj = !((sum - sum) == T(0));
+            if (I.edge && I.x0c + j >= nx) { ad = T(0); spj = T(0); }
+            added += ad;
+            sp = spj > sp ? spj : sp;
+            bad = bad || bj;
+        }
+        const bool st = I.out_lane && I.x0c >= 0 && I.x0c < nx;
+        ia.clamp += st ? added : T(0);
+        ia.smax = (st && sp > ia.smax) ? sp : ia.smax;
+        ia.bad = ia.bad || (st && bad);
+        if (st) {
+            const size_t o = (size_t)C * G.pitch + I.x0c;
+            st_vec<T, CPT>(A.e1 + o, oe);
+            st_vec<T, CPT>(A.u1 + o, ou);
+            st_vec<T, CPT>(A.v1 + o, ov);
+        }
+        if (I.edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                T ad = wetdry_fix(oe[j], ou[j], ov[j], n0.z[j], hd);
-                T spj = cfl_speed(oe[j], ou[j], ov[j], n0.z[j], G);
-                const T sum = oe[j] + ou[j] + ov[j];
-                const bool bj = !((sum - sum) == T(0));
-                if (edge && x0c + j >= nx) { ad = T(0); spj = T(0); }
-                added += ad;
-                sp = spj > sp ? spj : sp;
-                badc = badc || bj;
-            }
-            if (out_lane && x0c >= 0 && x0c < nx) {
-                clamp_i += added;
-                smax_i = sp > smax_i ? sp : smax_i;
-                bad_i = bad_i || badc;
-                const size_t o = (size_t)C * G.pitch + x0c;
-                st_vec<T, CPT>(A.e1 + o, oe);
-                st_vec<T, CPT>(A.u1 + o, ou);
-                st_vec<T, CPT>(A.v1 + o, ov);
-                if (edge) {
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
-                        const T qxn = (n0.e[j] - n0.z[j]) * n0.u[j];
-                        if (x0c + j == 0) bw_i += T(0.5) * (face_bnd(SIDE_W, qxn, G) + face_bnd(SIDE_W, qxs[j], G));
-                        if (x0c + j == nx - 1) be_i -= T(0.5) * (face_bnd(SIDE_E, qxn, G) + face_bnd(SIDE_E, qxs[j], G));
-                    }
-                }
-                if (C == 0 || C == ny - 1) {
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
-                        if (edge && x0c + j >= nx) continue;
-                        const T qyn = (n0.e[j] - n0.z[j]) * n0.v[j];
-                        if (C == 0) bs_i += T(0.5) * (face_bnd(SIDE_S, qyn, G) + face_bnd(SIDE_S, qys[j], G));
-                        if (C == ny - 1) bn_i -= T(0.5) * (face_bnd(SIDE_N, qyn, G) + face_bnd(SIDE_N, qys[j], G));
-                    }
-                }
+                const T qxn = h2[j] * R2.u[j];
+                const T w = T(0.5) * (face_bnd(SIDE_W, qxn, G) + face_bnd(SIDE_W, qx[j], G));
+                const T e = T(0.5) * (face_bnd(SIDE_E, qxn, G) + face_bnd(SIDE_E, qx[j], G));
+                ia.bw += (st && I.x0c + j == 0) ? w : T(0);
+                ia.be -= (st && I.x0c + j == nx - 1) ? e : T(0);
             }
         }
-        // rotate the register window
-        if (SY > 0) {
+        if (brow && (C == 0 || C == ny - 1)) {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) { PA.e[j] = PB.e[j]; PA.u[j] = PB.u[j]; PA.v[j] = PB.v[j]; }
+            for (int j = 0; j < CPT; ++j) {
+                const bool in = st && !(I.edge && I.x0c + j >= nx);
+                const T qyn = h2[j] * R2.v[j];
+                const T sv = T(0.5) * (face_bnd(SIDE_S, qyn, G) + face_bnd(SIDE_S, pc.qy[j], G));
+                const T nv = T(0.5) * (face_bnd(SIDE_N, qyn, G) + face_bnd(SIDE_N, pc.qy[j], G));
+                ia.bs += (in && C == 0) ? sv : T(0);
+                ia.bn -= (in && C == ny - 1) ? nv : T(0);
+            }
         }
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) { PB.e[j] = PN.e[j]; PB.u[j] = PN.u[j]; PB.v[j] = PN.v[j]; }
-        if (KAPPA) {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) { NA[j] = NB[j]; NB[j] = NN[j]; }
-        }
-        __syncwarp();
+    };
+
+    if (SY > 0) {  // the corrector reads P(C-1) from the buffer the predictor overwrites
+        if (k >= 4) corrector();
+        predictor();
+    } else {       // the corrector reads P(C+1), which the predictor produces
+        predictor();
+        if (k >= 4) corrector();
     }
-    if (timed_out) {
-        // drain this item's loads still in flight (bounded) before the ring is reused or left
-        const int issued = nr < waited + NPRE ? nr : waited + NPRE;
-        for (int k = waited; k < issued; ++k) {
-            const unsigned g = g0 + (unsigned)k;
-            unsigned long long t0 = clock64();
-            while (!mbar_try(bars + (g & (NSLOT - 1)), (g / NSLOT) & 1u))
-                if (clock64() - t0 > WAIT_LIMIT / 8) break;
-        }
-    }
-    g0 += (unsigned)nr;
-    acc.clamp += (double)clamp_i;
-    acc.bw += (double)bw_i; acc.be += (double)be_i; acc.bs += (double)bs_i; acc.bn += (double)bn_i;
-    acc.smax = fmax(acc.smax, (double)smax_i);
-    acc.bad = acc.bad || bad_i;
+    __syncwarp();
 }
 
 template <class T, int CPT, int SX, int SY, bool KAPPA>
-__global__ void __launch_bounds__(NWARP * 32, (sizeof(T) == 4 ? 4 : 2))
+__device__ __forceinline__ void run_item(const Args<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
+                                         Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
+                                         const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out) {
+    fence_async_smem();  // the previous item's rows were read through the generic proxy
+#pragma unroll
+    for (int k = 0; k < NPRE; ++k)
+        if (k < I.nr) issue_row<T, CPT>(I, k, tme, tmu, tmv, tmz);
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+        Cy.NY[0][j] = Cy.NY[1][j] = T(0);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) Cy.FY[0][f][j] = Cy.FY[1][f][j] = Cy.DX[0][f][j] = Cy.DX[1][f][j] = T(0);
+    }
+    ItemAcc<T> ia;
+    ia.clamp = ia.bw = ia.be = ia.bs = ia.bn = ia.smax = T(0);
+    ia.bad = false;
+    int k = 0;
+#pragma unroll 1
+    for (; k + 1 < I.nr; k += 2) {
+        row_step<T, CPT, SX, SY, KAPPA, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        if (timed_out) break;
+        row_step<T, CPT, SX, SY, KAPPA, 1>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        if (timed_out) break;
+    }
+    if (!timed_out && k < I.nr) {
+        row_step<T, CPT, SX, SY, KAPPA, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        ++k;
+    }
+    if (timed_out) {
+        // drain this item's loads still in flight (bounded) before the ring is reused or left
+        const int issued = I.nr < k + NPRE ? I.nr : k + NPRE;
+        for (int q = k; q < issued; ++q) {
+            const unsigned g = I.g0 + (unsigned)q;
+            unsigned long long t0 = clock64();
+            while (!mbar_try(I.bars + (g & (NSLOT - 1)), (g / NSLOT) & 1u))
+                if (clock64() - t0 > WAIT_LIMIT / 8) break;
+        }
+    }
+    I.g0 += (unsigned)I.nr;
+    acc.clamp += (double)ia.clamp;
+    acc.bw += (double)ia.bw; acc.be += (double)ia.be; acc.bs += (double)ia.bs; acc.bn += (double)ia.bn;
+    acc.smax = fmax(acc.smax, (double)ia.smax);
+    acc.bad = acc.bad || ia.bad;
+}
+
+template <class T, int CPT, int SX, int SY, bool KAPPA>
+__global__ void __launch_bounds__(NWARP * 32, Geo<T, CPT>::MINB)
 k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtensorMap tmu,
         const __grid_constant__ CUtensorMap tmv, const __grid_constant__ CUtensorMap tmz, const Args<T> A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -610,17 +682,31 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     acc.smax = 0.0;
     acc.bad = false;
     bool timed_out = false;
-    unsigned g0 = 0;
-    unsigned char* ring = smem + warp * Geo<T, CPT>::WARP_SMEM;
+    ItemCtx<T, CPT> I;
+    I.ring = smem + warp * Geo<T, CPT>::WARP_SMEM;
+    I.bars = bars[warp];
+    I.lane = lane;
+    I.out_lane = SX > 0 ? lane != 0 : lane != 31;
+    I.g0 = 0;
+    Carry<T, CPT> Cy;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+            Cy.P[b].e[j] = Cy.P[b].u[j] = Cy.P[b].v[j] = Cy.P[b].z[j] = Cy.P[b].qy[j] = T(0);
     const int gw = blockIdx.x * NWARP + warp, nw = gridDim.x * NWARP;
     for (int item = gw; item < A.nitems && !timed_out; item += nw) {
         const int kx = item % A.nxs, ky = item / A.nxs;
         const int x0 = kx * Geo<T, CPT>::OUT;
-        const int xw = SX > 0 ? x0 - CPT : x0;
-        const int y0 = ky * A.L;
-        const int y1 = min(A.G.ny, y0 + A.L);
-        run_item<T, CPT, SX, SY, KAPPA>(A, S, acc, ring, bars[warp], lane, xw, y0, y1, g0, &tme, &tmu, &tmv, &tmz,
-                                        timed_out);
+        I.xw = SX > 0 ? x0 - CPT : x0;
+        I.xb = (I.xw - 2) & ~(Geo<T, CPT>::ALIGN - 1);
+        I.col = (I.xw - I.xb) + CPT * lane;
+        I.x0c = I.xw + CPT * lane;
+        I.y0 = ky * A.L;
+        I.y1 = min(A.G.ny, I.y0 + A.L);
+        I.nr = I.y1 - I.y0 + 4;
+        I.edge = (I.xw - 2 < 0) || (I.xw + Geo<T, CPT>::W + 1 > A.G.nx - 1);
+        run_item<T, CPT, SX, SY, KAPPA>(A, S, acc, I, Cy, &tme, &tmu, &tmv, &tmz, timed_out);
     }
 
     // ---- reductions: warp, CTA, then one atomic per CTA

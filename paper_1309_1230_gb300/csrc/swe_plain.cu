@@ -137,9 +137,12 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, dou
             T ew = (i - 1 >= 0) ? face_eps(hxm1 > hd, wc, nu_switch(hxm2, hxm1, hc), nxc) : T(0);
             T en2 = (j + 1 < G.ny) ? face_eps(wc, hyp1 > hd, nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
             T es2 = (j - 1 >= 0) ? face_eps(hym1 > hd, wc, nu_switch(hym2, hym1, hc), nyc) : T(0);
-            en = dissip(en, e0, at(e, i - 1, j), at(e, i + 1, j), at(e, i, j - 1), at(e, i, j + 1), ee, ew, en2, es2, G.kappa);
-            un = dissip(un, u0, at(u, i - 1, j), at(u, i + 1, j), at(u, i, j - 1), at(u, i, j + 1), ee, ew, en2, es2, G.kappa);
-            vn = dissip(vn, v0, at(v, i - 1, j), at(v, i + 1, j), at(v, i, j - 1), at(v, i, j + 1), ee, ew, en2, es2, G.kappa);
+            en = dissip_faces(en, dflux(ee, at(e, i + 1, j), e0), dflux(ew, e0, at(e, i - 1, j)),
+                              dflux(en2, at(e, i, j + 1), e0), dflux(es2, e0, at(e, i, j - 1)), G.kappa);
+            un = dissip_faces(un, dflux(ee, at(u, i + 1, j), u0), dflux(ew, u0, at(u, i - 1, j)),
+                              dflux(en2, at(u, i, j + 1), u0), dflux(es2, u0, at(u, i, j - 1)), G.kappa);
+            vn = dissip_faces(vn, dflux(ee, at(v, i + 1, j), v0), dflux(ew, v0, at(v, i - 1, j)),
+                              dflux(en2, at(v, i, j + 1), v0), dflux(es2, v0, at(v, i, j - 1)), G.kappa);
         }
         // S16: fix, tallies
         added = wetdry_fix(en, un, vn, zc, G.h_dry);
