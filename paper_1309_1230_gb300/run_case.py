@@ -1,0 +1,61 @@
+"""Run one synthetic workload for a few steps through the C ABI.
+
+Used for profiler captures and quick throughput checks, e.g.
+
+    python -m paper_1309_1230_gb300.run_case --case river --n 4096 --steps 4
+    python -m paper_1309_1230_gb300.run_case --case dambreak --n 2048 --precision fp64 --kernel plain
+
+Prints one line with the step time measured with CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="river", choices=["river", "dambreak", "basin"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--kernel", default="fused", choices=["fused", "plain"])
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import inputs as I
+    from . import swe
+
+    if a.case == "river":
+        case = I.river(a.n, a.n)
+    elif a.case == "dambreak":
+        case = I.dam_break(a.n, a.n)
+    else:
+        case = I.basin_hump(a.n, a.n, manning_n=0.03, kappa=0.25)
+    prec = swe.SWE_FP32 if a.precision == "fp32" else swe.SWE_FP64
+    kern = swe.SWE_KERNEL_FUSED if a.kernel == "fused" else swe.SWE_KERNEL_PLAIN
+    s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=case["kappa"], bc=case["bc"],
+                   q_in=case["q_in"], precision=prec, kernel=kern)
+    s.set_bed(case["z"])
+    s.set_state(case["eta"], case["u"], case["v"])
+    s.step(a.warmup, want_info=False)
+    stream = torch.cuda.ExternalStream(s.stream_handle())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(a.steps, want_info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, a.steps)
+    info = s.info()
+    print(json.dumps({"case": a.case, "n": a.n, "precision": a.precision, "kernel": a.kernel, "steps": a.steps,
+                      "ms_per_step": ms, "cell_updates_per_s": case["nx"] * case["ny"] / (ms / 1e3),
+                      "volume": info.volume, "t": info.t, "time": time.time()}))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()
