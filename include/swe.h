@@ -169,6 +169,31 @@ void* swe_stream(const swe_ctx* ctx);
 /* Frees the context and every buffer it owns.  NULL is ignored. */
 void swe_destroy(swe_ctx* ctx);
 
+/* No-allocation FP32 step.  The paper has no counterpart to this entry point:
+ * it serves callers that cannot allocate device memory -- code that runs while
+ * a stream is being captured into a CUDA graph, engines whose device memory
+ * is all handed out by their own pool, loops that cannot wait on the
+ * allocator.  The caller passes device arrays (float, dense ny*nx, row-major)
+ * of the bed and the input state, and separate output arrays (no aliasing);
+ * the call queues one plain step (predictor and corrector kernels, the
+ * scheme of the header comment, uniform Manning n) on `stream` (NULL: the
+ * default stream) of the current device and allocates nothing.  Its scratch
+ * -- the predicted planes, the reduction control block and the step size --
+ * is one static device array of SWE_NOALLOC_MAX_CELLS cells (12 MB) that
+ * every GPU loading this library holds until the process exits; grids above
+ * that size are rejected with SWE_ERR_ARG.  dt_fixed > 0 gives the step size,
+ * 0 computes it from the CFL rule; dt_out (host, nullable) receives the step
+ * size used and then the call waits for the stream.  The predictor direction
+ * is that of step 0 of dir_cycle.  The first call on a device looks up the
+ * scratch's device address (once per device); make that first call before
+ * any stream capture.  Every call shares the one array and the previous
+ * call's contents are cleared or overwritten: calls that overlap on the GPU
+ * (other streams, other threads) race. */
+#define SWE_NOALLOC_MAX_CELLS (1 << 20)
+swe_status swe_step_plain_f32_noalloc(const swe_params* p, const float* z, const float* eta, const float* u,
+                                      const float* v, float* eta_out, float* u_out, float* v_out, double dt_fixed,
+                                      double* dt_out, void* stream);
+
 /* Text of the last failure on ctx (static text when ctx is NULL). */
 const char* swe_last_error(const swe_ctx* ctx);
 const char* swe_status_string(swe_status s);

@@ -453,3 +453,39 @@ cudaError_t swe_launch_call_begin(swe_ctx* c) {
     k_call_begin<<<1, 1, 0, c->stream>>>(c->ctl);
     return cudaGetLastError();
 }
+
+// One plain FP32 step on caller-provided dense buffers (row pitch `pitch`)
+// with caller-provided scratch: the predicted planes ps_*, a control block
+// (already cleared) and a dt slot.  compute_cfl: run the CFL reduction of the
+// input first; otherwise *dt_fixed (device) gives the step size.
+cudaError_t swe_plain_step_f32_raw(const swe_params* p, int pitch, const float* z, const float* e, const float* u,
+                                   const float* v, float* e1, float* u1, float* v1, float* ps_e, float* ps_u,
+                                   float* ps_v, DevCtl* ctl, const double* dt_fixed, double* dt_hist,
+                                   cudaStream_t st) {
+    GridK<float> G;
+    G.nx = p->nx; G.ny = p->ny; G.pitch = pitch;
+    G.g = (float)p->g; G.h_dry = (float)p->h_dry; G.kappa = (float)p->kappa;
+    G.gn2 = (float)(p->g * p->manning_n * p->manning_n);
+    G.inv_dx = (float)(1.0 / p->dx); G.inv_dy = (float)(1.0 / p->dy);
+    for (int s = 0; s < 4; ++s) { G.bc[s] = p->bc[s]; G.qin[s] = (float)p->q_in[s]; }
+    const size_t n = (size_t)p->nx * p->ny;
+    if (!dt_fixed) k_prologue<float><<<util_blocks(n), 256, 0, st>>>(G, e, u, v, z, ctl, 0);
+    k_plain_dt<<<1, 1, 0, st>>>(ctl, 0, 1, dt_fixed, 0, dt_hist, p->cfl, p->dt_max);
+    int sx, sy;
+    step_dirs(p->dir_cycle, 0, &sx, &sy);
+    dim3 blk(32, 8), grd((p->nx + 31) / 32, (p->ny + 7) / 8);
+    const double area = p->dx * p->dy;
+#define SWE_RAW_STEP(SX_, SY_)                                                                                   \
+    do {                                                                                                         \
+        k_plain_pred<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, p->dx, p->dy, p->g, e, u, v, z, nullptr,      \
+                                                           ps_e, ps_u, ps_v, ctl, area);                         \
+        k_plain_corr<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, p->dx, p->dy, p->g, e, u, v, z, nullptr,      \
+                                                           ps_e, ps_u, ps_v, e1, u1, v1, 1, area);               \
+    } while (0)
+    if (sx > 0 && sy > 0) SWE_RAW_STEP(1, 1);
+    else if (sx > 0) SWE_RAW_STEP(1, -1);
+    else if (sy > 0) SWE_RAW_STEP(-1, 1);
+    else SWE_RAW_STEP(-1, -1);
+#undef SWE_RAW_STEP
+    return cudaGetLastError();
+}

@@ -26,6 +26,7 @@ SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_OUTFLOW = 0, 1, 2
 SWE_FP64, SWE_FP32 = 0, 1
 SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN = 0, 1
 SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED = 1, 2, 4
+SWE_NOALLOC_MAX_CELLS = 1 << 20
 
 
 class swe_params(ctypes.Structure):
@@ -79,6 +80,8 @@ _SIGS = {
     "swe_stream": (ctypes.c_void_p, [_ctxp]),
     "swe_destroy": (None, [_ctxp]),
     "swe_last_error": (ctypes.c_char_p, [_ctxp]),
+    "swe_step_plain_f32_noalloc": (ctypes.c_int, [ctypes.POINTER(swe_params), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                  ctypes.c_double, _dp, _vp]),
     "swe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
