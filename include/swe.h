@@ -169,6 +169,30 @@ void* swe_stream(const swe_ctx* ctx);
 /* Frees the context and every buffer it owns.  NULL is ignored. */
 void swe_destroy(swe_ctx* ctx);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent scenarios of uneven grid size advanced together (FP32),
+ * each with its own CFL step: one persistent cooperative launch per
+ * swe_batch_step call, captured in a CUDA graph when use_graph is set.  The
+ * shared settings come from p (g, cfl, h_dry, dt_max, kappa, bc, q_in,
+ * dir_cycle 0 or 1, device, stream, seg_rows, use_graph, dry_skip; nx, ny
+ * and manning_n are ignored); count scenarios have sizes nx[i] x ny[i] and
+ * Manning n manning_n[i].  Host arrays per scenario are ny[i]*nx[i] doubles.
+ * Scenario i's results are bitwise those of a single-grid FP32 context with
+ * the same inputs.  An item of cells whose 3x3 neighbourhood of items is dry
+ * (and away from inflow sides) is skipped when dry_skip is set; dry cells of
+ * such a neighbourhood would not change.  infos (nullable) receives count
+ * step-info records.  precision must be SWE_FP32 (else SWE_ERR_UNSUPPORTED). */
+typedef struct swe_batch swe_batch;
+swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* nx, const int32_t* ny,
+                            const double* manning_n, swe_batch** out);
+swe_status swe_batch_set_bed(swe_batch* b, int32_t idx, const double* z);
+/* Same normalisation and errors as swe_set_state; the bed must be set first. */
+swe_status swe_batch_set_state(swe_batch* b, int32_t idx, const double* eta, const double* u, const double* v);
+swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos);
+swe_status swe_batch_get_state(swe_batch* b, int32_t idx, double* eta, double* u, double* v);
+void swe_batch_destroy(swe_batch* b);
+const char* swe_batch_last_error(const swe_batch* b);
+
 /* No-allocation FP32 step.  The paper has no counterpart to this entry point:
  * it serves callers that cannot allocate device memory -- code that runs while
  * a stream is being captured into a CUDA graph, engines whose device memory

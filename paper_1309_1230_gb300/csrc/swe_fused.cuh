@@ -59,11 +59,17 @@ struct Geo {
     static constexpr int MINB = (sizeof(T) == 4 && CPT <= 2) ? 16 : 8;  // CTAs per SM the registers must allow
 };
 
+// What one work item reads and writes: its scenario's constants and the
+// new-level planes, with pointers at the scenario's row 0.
 template <class T>
-struct Args {
+struct ItemIO {
     GridK<T> G;
-    T* e1; T* u1; T* v1;           // new level (pitched)
-    const T* n2;                   // per-cell g n^2 or null
+    T* e1; T* u1; T* v1;
+    const T* n2;
+};
+
+template <class T>
+struct Args : ItemIO<T> {
     DevCtl* ctl;
     const double* dt_fixed;        // null: CFL step
     double* dt_hist;
@@ -172,6 +178,7 @@ struct ItemCtx {
     unsigned char* ring;
     uint64_t* bars;
     int lane, xw, xb, col, x0c, y0, y1, nr;
+    int yoff;                    // tensor row of the scenario's row 0
     bool out_lane, edge;
     unsigned g0;
 };
@@ -231,7 +238,7 @@ __device__ __forceinline__ void issue_row(const ItemCtx<T, CPT>& I, int k, const
     const unsigned bar = saddr(I.bars + (g & (NSLOT - 1)));
     const unsigned dst = saddr(I.ring + (g & (NSLOT - 1)) * Gm::SLOT);
     const unsigned pred = I.lane == 0 ? 1u : 0u;
-    const int y = I.y0 - 2 + k;
+    const int y = I.yoff + I.y0 - 2 + k;
     asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}"
                  ::"r"(pred), "r"(bar), "r"(4u * Gm::BW * (unsigned)sizeof(T)) : "memory");
     const CUtensorMap* maps[4] = {tme, tmu, tmv, tmz};
@@ -266,7 +273,7 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 // predictor and x dissipation of row r-1, and the corrector, average,
 // dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.
 template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR>
-__device__ __forceinline__ void row_step(const Args<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
+__device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
                                          bool& timed_out) {
@@ -601,7 +608,7 @@ __device__ __forceinline__ void row_step(const Args<T>& A, const StepK<T>& S, co
 }
 
 template <class T, int CPT, int SX, int SY, bool KAPPA>
-__device__ __forceinline__ void run_item(const Args<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
+__device__ __forceinline__ void run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
                                          Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
                                          const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out) {
     fence_async_smem();  // the previous item's rows were read through the generic proxy
@@ -694,6 +701,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
             Cy.P[b].e[j] = Cy.P[b].u[j] = Cy.P[b].v[j] = Cy.P[b].z[j] = Cy.P[b].qy[j] = T(0);
+    I.yoff = 0;
     const int gw = blockIdx.x * NWARP + warp, nw = gridDim.x * NWARP;
     for (int item = gw; item < A.nitems && !timed_out; item += nw) {
         const int kx = item % A.nxs, ky = item / A.nxs;

@@ -83,6 +83,14 @@ _SIGS = {
     "swe_step_plain_f32_noalloc": (ctypes.c_int, [ctypes.POINTER(swe_params), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                   ctypes.c_double, _dp, _vp]),
     "swe_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "swe_batch_create": (ctypes.c_int, [ctypes.POINTER(swe_params), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), _dp, ctypes.POINTER(ctypes.c_void_p)]),
+    "swe_batch_set_bed": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+    "swe_batch_set_state": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, _dp]),
+    "swe_batch_step": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(swe_step_info)]),
+    "swe_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, _dp]),
+    "swe_batch_destroy": (None, [_vp]),
+    "swe_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 
@@ -263,3 +271,60 @@ def _torch_check(a, s: Solver):
     want = torch.float64 if s.params.precision == SWE_FP64 else torch.float32
     if not (a.is_cuda and a.dtype == want and a.is_contiguous() and tuple(a.shape) == s.shape):
         raise ValueError(f"expected a contiguous CUDA {want} tensor of shape {s.shape}")
+
+
+class Batch:
+    """Many scenarios advanced together (FP32): owns a swe_batch."""
+
+    def __init__(self, sizes, manning_n, **kw):
+        self.lib = load()
+        kw.setdefault("precision", SWE_FP32)
+        self.params = make_params(1, 1, **kw)
+        self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
+        n = len(self.sizes)
+        nx = (ctypes.c_int32 * n)(*[a for a, _ in self.sizes])
+        ny = (ctypes.c_int32 * n)(*[b for _, b in self.sizes])
+        mn = np.ascontiguousarray(manning_n, dtype=np.float64)
+        b = ctypes.c_void_p()
+        st = self.lib.swe_batch_create(ctypes.byref(self.params), n, nx, ny, _p(mn), ctypes.byref(b))
+        if st != SWE_OK:
+            raise SweError(st, "swe_batch_create failed: " + self.lib.swe_status_string(st).decode())
+        self.b = b
+        self.count = n
+
+    def _chk(self, st):
+        if st != SWE_OK:
+            raise SweError(st, self.lib.swe_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.swe_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self, i):
+        nx, ny = self.sizes[i]
+        return (ny, nx)
+
+    def set_bed(self, i, z):
+        self._chk(self.lib.swe_batch_set_bed(self.b, int(i), _p(_f64(z, self._shape(i)))))
+
+    def set_state(self, i, eta, u, v):
+        e, uu, vv = (_f64(a, self._shape(i)) for a in (eta, u, v))
+        self._chk(self.lib.swe_batch_set_state(self.b, int(i), _p(e), _p(uu), _p(vv)))
+
+    def step(self, nsteps, want_info=True):
+        infos = (swe_step_info * self.count)() if want_info else None
+        self._chk(self.lib.swe_batch_step(self.b, int(nsteps), infos))
+        return [_info(x) for x in infos] if want_info else None
+
+    def get_state(self, i):
+        sh = self._shape(i)
+        e, u, v = np.empty(sh), np.empty(sh), np.empty(sh)
+        self._chk(self.lib.swe_batch_get_state(self.b, int(i), _p(e), _p(u), _p(v)))
+        return e, u, v
