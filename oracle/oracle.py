@@ -136,6 +136,11 @@ class OracleLib:
         lib.orc_volume.restype = ctypes.c_double
         lib.orc_prepare_state.argtypes = [P, dp, dp, dp, dp]
         lib.orc_prepare_state.restype = ctypes.c_int
+        if hasattr(lib, "orc_adjoint"):
+            lp = ctypes.POINTER(ctypes.c_int64)
+            lib.orc_adjoint.argtypes = [P, dp, dp, dp, dp, dp, ctypes.c_int64, ctypes.c_int32, dp, lp,
+                                        ctypes.c_int32, dp, dp, dp, dp, dp, dp]
+            lib.orc_adjoint.restype = ctypes.c_int
         self.lib = lib
 
     def run(self, p: Params, z, eta, u, v, nsteps: int, *, nfield=None, step0: int = 0,
@@ -183,6 +188,34 @@ class OracleLib:
         return e, uu, vv
 
 
+class AdjointResult:
+    def __init__(self, loss, grad_n, grad_eta0, grad_u0, grad_v0, status):
+        self.loss, self.grad_n, self.grad_eta0 = loss, grad_n, grad_eta0
+        self.grad_u0, self.grad_v0, self.status = grad_u0, grad_v0, status
+
+
+def _adjoint(lib, p, z, nfield, eta, u, v, dt, gauges, obs, step0=0):
+    shape = (p.ny, p.nx)
+    z, nf = _arr(z, shape), _arr(nfield, shape)
+    e, uu, vv = _arr(eta, shape), _arr(u, shape), _arr(v, shape)
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    T = dt.shape[0]
+    g = np.ascontiguousarray(gauges, dtype=np.int64)
+    ob = np.ascontiguousarray(obs, dtype=np.float64).reshape(T, g.shape[0])
+    loss = np.zeros(1)
+    gn, ge, gu, gv = (np.zeros(shape) for _ in range(4))
+    pc = p._c()
+    st = lib.orc_adjoint(ctypes.byref(pc), _ptr(z), _ptr(nf), _ptr(e), _ptr(uu), _ptr(vv), int(step0), int(T),
+                         _ptr(dt), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(g.shape[0]), _ptr(ob),
+                         _ptr(loss), _ptr(gn), _ptr(ge), _ptr(gu), _ptr(gv))
+    if st == 1:
+        raise ValueError("oracle rejected the adjoint arguments")
+    return AdjointResult(float(loss[0]), gn, ge, gu, gv, st)
+
+
+OracleLib.adjoint = lambda self, *a, **k: _adjoint(self.lib, *a, **k)
+
+
 def _default() -> OracleLib:
     global _lib
     with _lock:
@@ -207,3 +240,10 @@ def volume(p: Params, z, eta) -> float:
 def prepare_state(p: Params, z, eta, u, v):
     """Set-state normalisation (see ``orc_prepare_state``); returns copies."""
     return _default().prepare_state(p, z, eta, u, v)
+
+
+def adjoint(p: Params, z, nfield, eta, u, v, dt, gauges, obs, step0: int = 0) -> AdjointResult:
+    """Discrete adjoint of nsteps = len(dt) steps with frozen step sizes:
+    gradient of L = 1/2 sum_k sum_g (eta_g^k - obs[k-1, g])^2 with respect to
+    the per-cell Manning n and the initial eta, u, v (kappa 0, fully wet)."""
+    return _default().adjoint(p, z, nfield, eta, u, v, dt, gauges, obs, step0)

@@ -561,3 +561,385 @@ int orc_prepare_state(const orc_params* p, const double* z, double* eta, double*
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint (reverse mode) of the step, for gradient checks    */
+/* ------------------------------------------------------------------ */
+/* Scope: dt frozen per step (the CFL minimum is not differentiated),
+ * kappa = 0 (S15 off) and a fully wet domain in every stage (S8/S16 are then
+ * the identity); orc_adjoint returns 5 otherwise.  Each forward sub-step
+ * below has its reverse: given the cotangent of its outputs it adds the
+ * cotangents of its inputs, over the same full-grid arrays. */
+enum { ORC_ERR_NOT_WET = 5 };
+
+typedef struct {
+    double *le, *lu, *lv, *lh;        /* level n (with ghosts) */
+    double *lC, *lfx, *lfy, *lqx, *lqy;
+    double *les, *lus, *lvs, *lhs;    /* predicted (with ghosts) */
+    double *lCs, *lfxs, *lfys, *lqxs, *lqys;
+    double *ln2;                      /* per cell */
+} adjw;
+
+static void adjw_free(adjw* a) {
+    void* ptrs[] = {a->le, a->lu, a->lv, a->lh, a->lC, a->lfx, a->lfy, a->lqx, a->lqy, a->les, a->lus,
+                    a->lvs, a->lhs, a->lCs, a->lfxs, a->lfys, a->lqxs, a->lqys, a->ln2};
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
+    memset(a, 0, sizeof(*a));
+}
+
+static int adjw_alloc(adjw* a, int nx, int ny) {
+    memset(a, 0, sizeof(*a));
+    size_t nc = (size_t)(nx + 2) * (size_t)(ny + 2);
+    size_t nfx = (size_t)(nx + 1) * (size_t)ny, nfy = (size_t)nx * (size_t)(ny + 1);
+    double** cells[] = {&a->le, &a->lu, &a->lv, &a->lh, &a->lC, &a->lqx, &a->lqy, &a->les, &a->lus,
+                        &a->lvs, &a->lhs, &a->lCs, &a->lqxs, &a->lqys, &a->ln2};
+    for (size_t k = 0; k < sizeof(cells) / sizeof(cells[0]); ++k)
+        if (!(*cells[k] = calloc(nc, sizeof(double)))) { adjw_free(a); return 0; }
+    if (!(a->lfx = calloc(nfx, sizeof(double))) || !(a->lfy = calloc(nfy, sizeof(double))) ||
+        !(a->lfxs = calloc(nfx, sizeof(double))) || !(a->lfys = calloc(nfy, sizeof(double)))) {
+        adjw_free(a);
+        return 0;
+    }
+    return 1;
+}
+
+static void adjw_zero(adjw* a, int nx, int ny) {
+    size_t nc = (size_t)(nx + 2) * (size_t)(ny + 2);
+    size_t nfx = (size_t)(nx + 1) * (size_t)ny, nfy = (size_t)nx * (size_t)(ny + 1);
+    double* cells[] = {a->le, a->lu, a->lv, a->lh, a->lC, a->lqx, a->lqy, a->les, a->lus, a->lvs, a->lhs,
+                       a->lCs, a->lqxs, a->lqys};
+    for (size_t k = 0; k < sizeof(cells) / sizeof(cells[0]); ++k) memset(cells[k], 0, nc * sizeof(double));
+    memset(a->lfx, 0, nfx * sizeof(double)); memset(a->lfy, 0, nfy * sizeof(double));
+    memset(a->lfxs, 0, nfx * sizeof(double)); memset(a->lfys, 0, nfy * sizeof(double));
+}
+
+/* reverse of fill_ghosts: fold the ghost cotangents into the adjacent cells */
+static void adj_ghosts(const orc_params* p, work* w, const double* h, double* le, double* lu, double* lv,
+                       double* lh) {
+    const int nx = w->nx, ny = w->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int side = SIDE_W; side <= SIDE_E; ++side) {
+            int ii = (side == SIDE_W) ? 0 : nx - 1, ig = (side == SIDE_W) ? -1 : nx;
+            double sgn = (side == SIDE_W) ? 1.0 : -1.0;
+            size_t a = G(ii, j), b = G(ig, j);
+            le[a] += le[b]; lh[a] += lh[b];
+            switch (p->bc[side]) {
+            case BC_WALL: lu[a] -= lu[b]; lv[a] += lv[b]; break;
+            case BC_INFLOW:
+                if (h[a] > p->h_dry) lh[a] += -sgn * p->q_in[side] / (h[a] * h[a]) * lu[b];
+                break;
+            default: lu[a] += lu[b]; lv[a] += lv[b]; break;
+            }
+            le[b] = lh[b] = lu[b] = lv[b] = 0.0;
+        }
+    for (int i = 0; i < nx; ++i)
+        for (int side = SIDE_S; side <= SIDE_N; ++side) {
+            int jj = (side == SIDE_S) ? 0 : ny - 1, jg = (side == SIDE_S) ? -1 : ny;
+            double sgn = (side == SIDE_S) ? 1.0 : -1.0;
+            size_t a = G(i, jj), b = G(i, jg);
+            le[a] += le[b]; lh[a] += lh[b];
+            switch (p->bc[side]) {
+            case BC_WALL: lv[a] -= lv[b]; lu[a] += lu[b]; break;
+            case BC_INFLOW:
+                if (h[a] > p->h_dry) lh[a] += -sgn * p->q_in[side] / (h[a] * h[a]) * lv[b];
+                break;
+            default: lu[a] += lu[b]; lv[a] += lv[b]; break;
+            }
+            le[b] = lh[b] = lu[b] = lv[b] = 0.0;
+        }
+}
+
+/* reverse of fluxes(): face cotangents to the cell fluxes, then to h, u, v */
+static void adj_fluxes(const orc_params* p, work* w, const double* h, const double* u, const double* v,
+                       const double* lfx, const double* lfy, double* lqx, double* lqy, double* lh, double* lu,
+                       double* lv, int sx, int sy) {
+    const int nx = w->nx, ny = w->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = -1; i < nx; ++i) {
+            double l = lfx[FX(i, j)];
+            if (i == -1 || i == nx - 1) {
+                int side = (i == -1) ? SIDE_W : SIDE_E, inner = (i == -1) ? 0 : nx - 1;
+                if (p->bc[side] == BC_OUTFLOW) lqx[G(inner, j)] += l;
+            } else {
+                lqx[(sx > 0) ? G(i + 1, j) : G(i, j)] += l;
+            }
+        }
+    for (int j = -1; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double l = lfy[FY(i, j)];
+            if (j == -1 || j == ny - 1) {
+                int side = (j == -1) ? SIDE_S : SIDE_N, inner = (j == -1) ? 0 : ny - 1;
+                if (p->bc[side] == BC_OUTFLOW) lqy[G(i, inner)] += l;
+            } else {
+                lqy[(sy > 0) ? G(i, j + 1) : G(i, j)] += l;
+            }
+        }
+    for (int j = -1; j <= ny; ++j)
+        for (int i = -1; i <= nx; ++i) {
+            int gi = (i < 0 || i >= nx), gj = (j < 0 || j >= ny);
+            if (gi && gj) continue;
+            size_t c = G(i, j);
+            lh[c] += u[c] * lqx[c] + v[c] * lqy[c];
+            lu[c] += h[c] * lqx[c];
+            lv[c] += h[c] * lqy[c];
+        }
+}
+
+/* reverse of continuity() */
+static void adj_continuity(work* w, double dt, double dx, double dy, const double* lout, double* leta_n,
+                           double* lfx, double* lfy) {
+    const int nx = w->nx, ny = w->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double l = lout[G(i, j)];
+            leta_n[G(i, j)] += l;
+            lfx[FX(i, j)] -= dt / dx * l;
+            lfx[FX(i - 1, j)] += dt / dx * l;
+            lfy[FY(i, j)] -= dt / dy * l;
+            lfy[FY(i, j - 1)] += dt / dy * l;
+        }
+}
+
+/* reverse of friction(): C = g n2 |U| / h^(4/3) on wet cells */
+static void adj_friction(const orc_params* p, work* w, const double* h, const unsigned char* wet,
+                         const double* u, const double* v, const double* C, const double* lC, double* lh,
+                         double* lu, double* lv, double* ln2) {
+    const int nx = w->nx, ny = w->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = G(i, j);
+            if (!wet[c]) continue;
+            double mag = sqrt(u[c] * u[c] + v[c] * v[c]);
+            double P = pow(h[c], 4.0 / 3.0);
+            double l = lC[c];
+            ln2[c] += p->g * mag / P * l;
+            if (mag > 0.0) {
+                lu[c] += p->g * w->n2[c] * (u[c] / mag) / P * l;
+                lv[c] += p->g * w->n2[c] * (v[c] / mag) / P * l;
+            }
+            lh[c] += -(4.0 / 3.0) * C[c] / h[c] * l;
+        }
+}
+
+/* reverse of momentum() */
+static void adj_momentum(const orc_params* p, work* w, double dt, int sx, int sy, const double* eta,
+                         const double* u, const double* v, const unsigned char* wet, const double* C,
+                         const double* u_out, const double* v_out, const double* lu_out, const double* lv_out,
+                         double* leta, double* lu, double* lv, double* lC, double* lu_n, double* lv_n) {
+    const int nx = w->nx, ny = w->ny;
+    const double* z = w->z;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = G(i, j);
+            size_t xn = (sx > 0) ? G(i + 1, j) : G(i - 1, j);
+            size_t yn = (sy > 0) ? G(i, j + 1) : G(i, j - 1);
+            int xwall = (!wet[xn] && z[xn] > eta[c]), ywall = (!wet[yn] && z[yn] > eta[c]);
+            double ex = xwall ? eta[c] : eta[xn], ey = ywall ? eta[c] : eta[yn];
+            (void)ex; (void)ey;
+            double dux = sx * (u[xn] - u[c]), dvx = sx * (v[xn] - v[c]);
+            double duy = sy * (u[yn] - u[c]), dvy = sy * (v[yn] - v[c]);
+            double den = 1.0 + dt * C[c];
+            double lo_u = lu_out[c], lo_v = lv_out[c];
+            lu_n[c] += lo_u / den;
+            lv_n[c] += lo_v / den;
+            double lAu = -dt * lo_u / den, lAv = -dt * lo_v / den;
+            double lden = -(u_out[c] * lo_u + v_out[c] * lo_v) / den;
+            lC[c] += dt * lden;
+            double ldux = u[c] / p->dx * lAu, lduy = v[c] / p->dy * lAu, ldex = p->g / p->dx * lAu;
+            double ldvx = u[c] / p->dx * lAv, ldvy = v[c] / p->dy * lAv, ldey = p->g / p->dy * lAv;
+            lu[c] += dux / p->dx * lAu + dvx / p->dx * lAv;
+            lv[c] += duy / p->dy * lAu + dvy / p->dy * lAv;
+            lu[xn] += sx * ldux; lu[c] -= sx * ldux;
+            lv[xn] += sx * ldvx; lv[c] -= sx * ldvx;
+            lu[yn] += sy * lduy; lu[c] -= sy * lduy;
+            lv[yn] += sy * ldvy; lv[c] -= sy * ldvy;
+            double lex = sx * ldex, ley = sy * ldey;
+            leta[c] -= sx * ldex + sy * ldey;
+            if (xwall) leta[c] += lex; else leta[xn] += lex;
+            if (ywall) leta[c] += ley; else leta[yn] += ley;
+        }
+}
+
+static int all_wet(work* w, const unsigned char* wet) {
+    for (int j = 0; j < w->ny; ++j)
+        for (int i = 0; i < w->nx; ++i)
+            if (!wet[G(i, j)]) return 0;
+    return 1;
+}
+
+/* Forward sub-steps S1-S14 of step k from the current w->eta/u/v, keeping
+ * every intermediate in w; the new level is in w->e1/u1/v1 (S15 off, S16 the
+ * identity when fully wet).  Returns 0, or ORC_ERR_NOT_WET. */
+static int fwd_keep(const orc_params* p, work* w, int64_t k, double dt, int* sx, int* sy) {
+    const int ny = w->ny;
+    step_dirs(p->dir_cycle, k, sx, sy);
+    depth_mask(p, w);
+    if (!all_wet(w, w->wet)) return ORC_ERR_NOT_WET;
+    fill_ghosts(p, w, w->eta, w->u, w->v, w->h, w->wet);
+    fluxes(p, w, w->h, w->u, w->v, w->qx, w->qy, w->fx, w->fy, *sx, *sy);
+    continuity(w, dt, p->dx, p->dy, w->eta, w->fx, w->fy, w->es);
+    friction(p, w, w->h, w->wet, w->u, w->v, w->C);
+    momentum(p, w, dt, *sx, *sy, w->eta, w->u, w->v, w->wet, w->C, w->u, w->v, w->us, w->vs);
+    wetdry_fix(p, w, w->es, w->us, w->vs, w->hs, w->wets, w->row_a);
+    if (sum_rows(w->row_a, ny) != 0.0 || !all_wet(w, w->wets)) return ORC_ERR_NOT_WET;
+    fill_ghosts(p, w, w->es, w->us, w->vs, w->hs, w->wets);
+    fluxes(p, w, w->hs, w->us, w->vs, w->qxs, w->qys, w->fxs, w->fys, -*sx, -*sy);
+    continuity(w, dt, p->dx, p->dy, w->eta, w->fxs, w->fys, w->ess);
+    friction(p, w, w->hs, w->wets, w->us, w->vs, w->Cs);
+    momentum(p, w, dt, -*sx, -*sy, w->es, w->us, w->vs, w->wets, w->Cs, w->u, w->v, w->uss, w->vss);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < w->nx; ++i) {
+            size_t c = G(i, j);
+            w->e1[c] = 0.5 * (w->es[c] + w->ess[c]);
+            w->u1[c] = 0.5 * (w->us[c] + w->uss[c]);
+            w->v1[c] = 0.5 * (w->vs[c] + w->vss[c]);
+            if (!(w->e1[c] - w->z[c] > p->h_dry)) return ORC_ERR_NOT_WET;
+        }
+    return ORC_OK;
+}
+
+/* Reverse of one step: given the cotangent (le1, lu1, lv1) of level n+1 in
+ * the interior of a->le/lu/lv... the caller passes them in lin_*; on return
+ * a->le/lu/lv hold the cotangent of level n and a->ln2 has accumulated the
+ * cotangent of n^2 (per cell). */
+static void adj_step(const orc_params* p, work* w, adjw* a, double dt, int sx, int sy, const double* le1,
+                     const double* lu1, const double* lv1) {
+    const int nx = w->nx, ny = w->ny;
+    double* ln2 = a->ln2;
+    adjw_zero(a, nx, ny);
+    /* S14: average; the predicted state receives half directly */
+    double *less = calloc((size_t)(nx + 2) * (ny + 2), sizeof(double));
+    double *luss = calloc((size_t)(nx + 2) * (ny + 2), sizeof(double));
+    double *lvss = calloc((size_t)(nx + 2) * (ny + 2), sizeof(double));
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = G(i, j);
+            size_t k = (size_t)j * nx + i;
+            a->les[c] += 0.5 * le1[k]; less[c] = 0.5 * le1[k];
+            a->lus[c] += 0.5 * lu1[k]; luss[c] = 0.5 * lu1[k];
+            a->lvs[c] += 0.5 * lv1[k]; lvss[c] = 0.5 * lv1[k];
+        }
+    /* S13: corrector momentum (differenced state: predicted; base: level n) */
+    adj_momentum(p, w, dt, -sx, -sy, w->es, w->us, w->vs, w->wets, w->Cs, w->uss, w->vss, luss, lvss,
+                 a->les, a->lus, a->lvs, a->lCs, a->lu, a->lv);
+    /* S12: corrector friction */
+    adj_friction(p, w, w->hs, w->wets, w->us, w->vs, w->Cs, a->lCs, a->lhs, a->lus, a->lvs, ln2);
+    /* S11: corrector continuity */
+    adj_continuity(w, dt, p->dx, p->dy, less, a->le, a->lfxs, a->lfys);
+    /* S10: corrector fluxes */
+    adj_fluxes(p, w, w->hs, w->us, w->vs, a->lfxs, a->lfys, a->lqxs, a->lqys, a->lhs, a->lus, a->lvs, -sx, -sy);
+    /* S9: ghosts of the predicted state */
+    adj_ghosts(p, w, w->hs, a->les, a->lus, a->lvs, a->lhs);
+    /* S8: the fix is the identity (wet, no clamp); h* = eta* - z */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->les[c] += a->lhs[c]; }
+    /* S7: predictor momentum (differenced and base state: level n) */
+    adj_momentum(p, w, dt, sx, sy, w->eta, w->u, w->v, w->wet, w->C, w->us, w->vs, a->lus, a->lvs,
+                 a->le, a->lu, a->lv, a->lC, a->lu, a->lv);
+    /* S6: predictor friction */
+    adj_friction(p, w, w->h, w->wet, w->u, w->v, w->C, a->lC, a->lh, a->lu, a->lv, ln2);
+    /* S5: predictor continuity */
+    adj_continuity(w, dt, p->dx, p->dy, a->les, a->le, a->lfx, a->lfy);
+    /* S4: predictor fluxes */
+    adj_fluxes(p, w, w->h, w->u, w->v, a->lfx, a->lfy, a->lqx, a->lqy, a->lh, a->lu, a->lv, sx, sy);
+    /* S3: ghosts of level n */
+    adj_ghosts(p, w, w->h, a->le, a->lu, a->lv, a->lh);
+    /* S1: h = eta - z */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->le[c] += a->lh[c]; }
+    free(less); free(luss); free(lvss);
+}
+
+/* Gradient of L = 1/2 sum_{k=1..T} sum_g (eta_g^k - obs[k-1][g])^2 with
+ * respect to the per-cell Manning n field and the initial eta (and u, v),
+ * by the discrete adjoint of T steps from step index step0 with the given
+ * frozen step sizes.  Returns 0, 1 (bad argument), 3 (non-finite) or 5 (a
+ * stage was not fully wet, or kappa != 0). */
+int orc_adjoint(const orc_params* p, const double* z, const double* nfield, const double* eta0,
+                const double* u0, const double* v0, int64_t step0, int32_t T, const double* dt,
+                const int64_t* gauges, int32_t ng, const double* obs, double* loss, double* grad_n,
+                double* grad_eta0, double* grad_u0, double* grad_v0) {
+    if (!check_params(p) || !z || !nfield || !eta0 || !u0 || !v0 || !dt || T < 0 || ng < 0 || !loss) return ORC_ERR_ARG;
+    if (p->kappa != 0.0) return ORC_ERR_NOT_WET;
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)nx * ny, nc = (size_t)(nx + 2) * (ny + 2);
+    for (int32_t g = 0; g < ng; ++g)
+        if (gauges[g] < 0 || (size_t)gauges[g] >= n) return ORC_ERR_ARG;
+    work wk, *w = &wk;
+    if (!work_alloc(w, nx, ny)) return ORC_ERR_ARG;
+    adjw aw, *a = &aw;
+    if (!adjw_alloc(a, nx, ny)) { work_free(w); return ORC_ERR_ARG; }
+    /* forward, keeping every level (interior, dense) */
+    double* st = malloc((size_t)(T + 1) * 3 * n * sizeof(double));
+    double *le1 = malloc(n * sizeof(double)), *lu1 = malloc(n * sizeof(double)), *lv1 = malloc(n * sizeof(double));
+    double* gn = calloc(nc, sizeof(double));
+    if (!st || !le1 || !lu1 || !lv1 || !gn) { free(st); free(le1); free(lu1); free(lv1); free(gn); adjw_free(a); work_free(w); return ORC_ERR_ARG; }
+    load(p, w, z, nfield, eta0, u0, v0);
+    int rc = ORC_OK;
+    double L = 0.0;
+    for (int32_t s = 0; s <= T && rc == ORC_OK; ++s) {
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = G(i, j), k = (size_t)j * nx + i;
+                st[(size_t)s * 3 * n + k] = w->eta[c];
+                st[(size_t)s * 3 * n + n + k] = w->u[c];
+                st[(size_t)s * 3 * n + 2 * n + k] = w->v[c];
+            }
+        if (s >= 1)
+            for (int32_t g = 0; g < ng; ++g) {
+                double r = st[(size_t)s * 3 * n + gauges[g]] - obs[(size_t)(s - 1) * ng + g];
+                L += 0.5 * r * r;
+            }
+        if (s == T) break;
+        int sx, sy;
+        rc = fwd_keep(p, w, step0 + s, dt[s], &sx, &sy);
+        double* t;
+        t = w->eta; w->eta = w->e1; w->e1 = t;
+        t = w->u; w->u = w->u1; w->u1 = t;
+        t = w->v; w->v = w->v1; w->v1 = t;
+    }
+    if (rc == ORC_OK && !isfinite(L)) rc = ORC_ERR_NONFINITE;
+    if (rc == ORC_OK) {
+        *loss = L;
+        /* cotangent of level T: the gauge residuals */
+        memset(le1, 0, n * sizeof(double)); memset(lu1, 0, n * sizeof(double)); memset(lv1, 0, n * sizeof(double));
+        if (T >= 1)
+            for (int32_t g = 0; g < ng; ++g)
+                le1[gauges[g]] += st[(size_t)T * 3 * n + gauges[g]] - obs[(size_t)(T - 1) * ng + g];
+        for (int32_t s = T - 1; s >= 0; --s) {
+            /* recompute step s from level s, then reverse it */
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t c = G(i, j), k = (size_t)j * nx + i;
+                    w->eta[c] = st[(size_t)s * 3 * n + k];
+                    w->u[c] = st[(size_t)s * 3 * n + n + k];
+                    w->v[c] = st[(size_t)s * 3 * n + 2 * n + k];
+                }
+            int sx, sy;
+            fwd_keep(p, w, step0 + s, dt[s], &sx, &sy);
+            memset(a->ln2, 0, nc * sizeof(double));
+            adj_step(p, w, a, dt[s], sx, sy, le1, lu1, lv1);
+            for (size_t c = 0; c < nc; ++c) gn[c] += a->ln2[c];
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    size_t c = G(i, j), k = (size_t)j * nx + i;
+                    le1[k] = a->le[c]; lu1[k] = a->lu[c]; lv1[k] = a->lv[c];
+                }
+            if (s >= 1)
+                for (int32_t g = 0; g < ng; ++g)
+                    le1[gauges[g]] += st[(size_t)s * 3 * n + gauges[g]] - obs[(size_t)(s - 1) * ng + g];
+        }
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = G(i, j), k = (size_t)j * nx + i;
+                if (grad_n) grad_n[k] = gn[c] * 2.0 * nfield[k];  /* d(n^2)/dn */
+                if (grad_eta0) grad_eta0[k] = le1[k];
+                if (grad_u0) grad_u0[k] = lu1[k];
+                if (grad_v0) grad_v0[k] = lv1[k];
+            }
+    }
+    free(st); free(le1); free(lu1); free(lv1); free(gn);
+    adjw_free(a);
+    work_free(w);
+    return rc;
+}
