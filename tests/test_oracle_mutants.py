@@ -75,9 +75,11 @@ def _first_failing_pin(lib):
 def test_pins_reject_planted_mistake(oracle, tmp_path, name):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    # the forward step comes first in the file; the adjoint's recompute of it
+    # repeats a few lines, which stay correct
+    assert src.count(old) >= 1, f"mutation site missing: {old!r}"
     mutated = tmp_path / "swe_oracle_mutant.c"
-    mutated.write_text(src.replace(old, new))
+    mutated.write_text(src.replace(old, new, 1))
     so = oracle.compile_source(str(mutated), str(tmp_path / "libmutant.so"))
     lib = oracle.OracleLib(so)
     assert _first_failing_pin(lib) is not None, f"no pin rejects the mistake '{name}'"
