@@ -169,6 +169,21 @@ void* swe_stream(const swe_ctx* ctx);
 /* Frees the context and every buffer it owns.  NULL is ignored. */
 void swe_destroy(swe_ctx* ctx);
 
+/* Discrete adjoint (reverse mode) of nsteps steps from the current state: the
+ * loss L = 1/2 sum_{k=1..nsteps} sum_g (eta_g^k - obs[(k-1)*ngauges + g])^2 at
+ * the gauge cells gauges[g] (index j*nx+i), and its gradient with respect to
+ * the per-cell Manning n (grad_n, host, ny*nx; the uniform manning_n counts
+ * as a field) and to the initial elevation (grad_eta0, host, ny*nx); both
+ * nullable.  The step sizes are those of the forward run and are held fixed
+ * (the CFL minimum is not differentiated).  Requires kappa = 0
+ * (SWE_ERR_UNSUPPORTED otherwise); the derivative is that of the smooth,
+ * fully wet branch of the wet/dry fixes.  The forward states are kept every
+ * checkpoint_every steps (0: ceil(sqrt(nsteps))) and recomputed per segment.
+ * Advances the context by nsteps steps (the forward run) and allocates its
+ * working buffers for the duration of the call. */
+swe_status swe_adjoint(swe_ctx* ctx, int32_t nsteps, const int64_t* gauges, int32_t ngauges, const double* obs,
+                       int32_t checkpoint_every, double* loss, double* grad_n, double* grad_eta0);
+
 /* ---------------------------------------------------------------- batches
  * Many independent scenarios of uneven grid size advanced together (FP32),
  * each with its own CFL step: one persistent cooperative launch per

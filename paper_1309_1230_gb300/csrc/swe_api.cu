@@ -209,6 +209,9 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
     if ((e = cudaMalloc(&c->bad_flag, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc");
     c->cur = 0;
     c->step = 0;
+    // the set-up memsets ran on the legacy default stream, which the
+    // context's non-blocking stream does not wait for
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "cudaDeviceSynchronize");
     *out = c;
     if (ensure_hist(c, 1024) != SWE_OK) { swe_destroy(c); *out = nullptr; return SWE_ERR_CUDA; }
     return SWE_OK;

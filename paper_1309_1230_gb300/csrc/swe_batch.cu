@@ -582,6 +582,8 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
     const int per_sm = occupancy_batch(p->kappa != 0.0);
     if (per_sm < 1) return bail("occupancy", cudaErrorInvalidConfiguration);
     b->grid = sms * per_sm;
+    // the set-up memsets and copies ran on the legacy default stream
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail("cudaDeviceSynchronize", e);
     *out = b;
     return SWE_OK;
 }

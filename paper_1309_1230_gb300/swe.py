@@ -91,6 +91,8 @@ _SIGS = {
     "swe_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, _dp]),
     "swe_batch_destroy": (None, [_vp]),
     "swe_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "swe_adjoint": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _dp,
+                                   ctypes.c_int32, _dp, _dp, _dp]),
 }
 
 
@@ -250,6 +252,18 @@ class Solver:
         i = swe_step_info()
         _check(self.lib.swe_get_info(self.ctx, ctypes.byref(i)), self.ctx)
         return _info(i)
+
+    def adjoint(self, nsteps: int, gauges, obs, checkpoint_every: int = 0):
+        """Loss and its gradient w.r.t. the Manning field and the initial
+        elevation over nsteps steps from the current state (advances it)."""
+        g = np.ascontiguousarray(gauges, dtype=np.int64)
+        ob = np.ascontiguousarray(obs, dtype=np.float64).reshape(int(nsteps), g.shape[0])
+        loss = np.zeros(1)
+        gn, ge = np.zeros(self.shape), np.zeros(self.shape)
+        st = self.lib.swe_adjoint(self.ctx, int(nsteps), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  int(g.shape[0]), _p(ob), int(checkpoint_every), _p(loss), _p(gn), _p(ge))
+        _check(st, self.ctx)
+        return float(loss[0]), gn, ge
 
     # torch tensors on the context's device, of the context's real type
     def set_state_device(self, eta, u, v):

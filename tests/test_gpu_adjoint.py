@@ -1,0 +1,131 @@
+"""GPU discrete adjoint: against the FP64 oracle's adjoint (1e-10 relative),
+against central differences of the GPU's own forward runs with the same
+frozen step sizes (1e-5 relative, FP64), FP32 against FP64, checkpoint
+spacing not changing the result, and the torch.autograd.Function."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1309_1230_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(nx=32, ny=28, seed=4, bc=(0, 0, 0, 0), q_in=(0.0,) * 4):
+    c = I.adjoint_case(nx, ny, seed=seed, n_gauges=6)
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    c["u"] = 0.05 * rng.standard_normal((ny, nx))
+    c["v"] = 0.05 * rng.standard_normal((ny, nx))
+    c["bc"], c["q_in"] = bc, q_in
+    nfield = 0.03 * (1.0 + 0.2 * rng.uniform(-1, 1, (ny, nx)))
+    return c, nfield
+
+
+def _solver(c, nfield, precision):
+    from paper_1309_1230_gb300 import swe
+    s = swe.Solver(c["nx"], c["ny"], manning_n=0.03, kappa=0.0, bc=c["bc"], q_in=c["q_in"], precision=precision)
+    s.set_bed(c["z"], nfield)
+    s.set_state(c["eta"], c["u"], c["v"])
+    return s
+
+
+def _obs(c, T, seed=9):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.stack([c["eta"].ravel()[c["gauges"]] + 0.01 * rng.standard_normal(len(c["gauges"])) for _ in range(T)])
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("bcs", ["walls", "open"])
+def test_gpu_adjoint_matches_oracle_adjoint(oracle, bcs):
+    from paper_1309_1230_gb300 import swe
+    bc, q = ((0, 0, 0, 0), (0.0,) * 4) if bcs == "walls" else ((1, 2, 0, 2), (0.4, 0.0, 0.0, 0.0))
+    c, nfield = _case(bc=bc, q_in=q)
+    T = 40
+    obs = _obs(c, T)
+    s = _solver(c, nfield, swe.SWE_FP64)
+    loss, gn, ge = s.adjoint(T, c["gauges"], obs)
+    s.close()
+    p = oracle.Params(nx=c["nx"], ny=c["ny"], manning_n=0.03, kappa=0.0, bc=bc, q_in=q)
+    fwd = oracle.run(p, c["z"], c["eta"], c["u"], c["v"], T, nfield=nfield)
+    ref = oracle.adjoint(p, c["z"], nfield, c["eta"], c["u"], c["v"], fwd.dt, c["gauges"], obs)
+    assert ref.status == 0
+    assert loss == pytest.approx(ref.loss, rel=1e-10)
+    assert _rel(gn, ref.grad_n) <= 1e-10
+    assert _rel(ge, ref.grad_eta0) <= 1e-10
+
+
+def test_gpu_adjoint_matches_central_differences():
+    from paper_1309_1230_gb300 import swe
+    c, nfield = _case()
+    T = 40
+    obs = _obs(c, T)
+    s = _solver(c, nfield, swe.SWE_FP64)
+    _, dts = s.step(T, want_dt=True)
+    s.close()
+    s = _solver(c, nfield, swe.SWE_FP64)
+    loss, gn, ge = s.adjoint(T, c["gauges"], obs)
+    s.close()
+
+    def L(nf, eta):
+        q = swe.Solver(c["nx"], c["ny"], manning_n=0.03, kappa=0.0, precision=swe.SWE_FP64)
+        q.set_bed(c["z"], nf)
+        q.set_state(eta, c["u"], c["v"])
+        tot = 0.0
+        for k in range(T):
+            q.step(1, dt_fixed=dts[k:k + 1], want_info=False)
+            e, _, _ = q.get_state()
+            r = e.ravel()[c["gauges"]] - obs[k]
+            tot += 0.5 * float(r @ r)
+        q.close()
+        return tot
+
+    assert loss == pytest.approx(L(nfield, c["eta"]), rel=1e-12)
+    rng = np.random.Generator(np.random.PCG64(3))
+    for _ in range(3):
+        dn = rng.standard_normal(nfield.shape) * 0.003
+        de = rng.standard_normal(nfield.shape) * 0.01
+        eps = 1e-5
+        fd = (L(nfield + eps * dn, c["eta"] + eps * de) - L(nfield - eps * dn, c["eta"] - eps * de)) / (2 * eps)
+        ad = float(np.sum(gn * dn) + np.sum(ge * de))
+        assert abs(fd - ad) <= 1e-5 * abs(fd), (fd, ad)
+
+
+def test_gpu_adjoint_fp32_and_checkpoint_spacing():
+    from paper_1309_1230_gb300 import swe
+    c, nfield = _case()
+    T = 40
+    obs = _obs(c, T)
+    res = {}
+    for prec, every in ((swe.SWE_FP64, 0), (swe.SWE_FP64, 1), (swe.SWE_FP64, 7), (swe.SWE_FP32, 0)):
+        s = _solver(c, nfield, prec)
+        res[(prec, every)] = s.adjoint(T, c["gauges"], obs, checkpoint_every=every)
+        s.close()
+    a = res[(swe.SWE_FP64, 0)]
+    for every in (1, 7):  # same arithmetic, other checkpoints: bitwise
+        b = res[(swe.SWE_FP64, every)]
+        assert b[0] == a[0] and np.array_equal(b[1], a[1]) and np.array_equal(b[2], a[2])
+    f = res[(swe.SWE_FP32, 0)]
+    assert f[0] == pytest.approx(a[0], rel=1e-3)
+    assert _rel(f[1], a[1]) <= 2e-2 and _rel(f[2], a[2]) <= 2e-2
+
+
+def test_autograd_function():
+    import torch
+    from paper_1309_1230_gb300 import autograd as A
+    c, nfield = _case()
+    T = 20
+    obs = _obs(c, T)
+    n_t = torch.tensor(nfield, dtype=torch.float64, requires_grad=True)
+    e_t = torch.tensor(c["eta"], dtype=torch.float64, requires_grad=True)
+    loss = A.gauge_misfit(n_t, e_t, c, T, c["gauges"], obs)
+    loss.backward()
+    from paper_1309_1230_gb300 import swe
+    s = _solver(c, nfield, swe.SWE_FP64)
+    l2, gn, ge = s.adjoint(T, c["gauges"], obs)
+    s.close()
+    assert float(loss.detach()) == l2
+    assert np.array_equal(n_t.grad.numpy(), gn) and np.array_equal(e_t.grad.numpy(), ge)
