@@ -42,7 +42,8 @@ BYTES_PER_CELL_FP32 = 28  # read eta, u, v, z; write eta, u, v (4 B each)
 WORKLOAD = "river reach 8192x8192 FP32, bed slope 1e-3 + seeded noise 0.5 m, inflow 2 m^2/s W, outflow E, walls S/N, n=0.03, kappa=0.25, CFL 0.5"
 METRIC = "cell-updates/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_step_river_fp32.md")
-FUSED_SOURCES = ["paper_1309_1230_gb300/csrc/swe_fused.cuh", "paper_1309_1230_gb300/csrc/swe_cell.cuh"]
+FUSED_SOURCES = ["paper_1309_1230_gb300/csrc/swe_fused.cuh", "paper_1309_1230_gb300/csrc/swe_cell.cuh",
+                 "paper_1309_1230_gb300/csrc/swe_fused.cu"]
 
 
 def sources_sha() -> str:
@@ -204,6 +205,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- rows per work item from the autotuner (on the live state, which it restores)
+    tuned_rows, tune_table = s.autotune(probe_steps=10)
+
     # ---- device-resident timing: W warm-up steps, then exactly K steps
     s.step(args.warmup, want_info=False)
     barrier()
@@ -272,6 +276,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": f"{NX}x{NY}", "cells": cells, "precision": "FP32 state, FP64 dt and tallies",
                        "l2": "inputs larger than L2 (1.07 GB state read per step)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "rows_per_item": tuned_rows,
+                       "autotune_ms_per_step": {str(k): round(v, 4) for k, v in tune_table.items()},
                        "t_end_s": info.t, "dt_last_s": info.dt_last},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],

@@ -184,6 +184,25 @@ void swe_destroy(swe_ctx* ctx);
 swe_status swe_adjoint(swe_ctx* ctx, int32_t nsteps, const int64_t* gauges, int32_t ngauges, const double* obs,
                        int32_t checkpoint_every, double* loss, double* grad_n, double* grad_eta0);
 
+/* Work-item autotuner of the fused step (the kernel's only shape parameter is
+ * the number of rows per work item, seg_rows; an item is one warp's column
+ * strip of 62 cells by that many rows).  swe_autotune_candidates writes the
+ * built-in candidate list (heights giving about 1 to 8 items per resident
+ * warp, and 32 and 64 rows) into rows[0..cap) and returns its length, or
+ * minus a status.  swe_autotune times each candidate (rows[0..nrows), or the
+ * built-in list when rows is NULL) on the context's current state: one
+ * warm-up step, then probe_steps steps timed with CUDA events on the
+ * context's stream; ms_per_step (nullable; needs rows) receives the time per
+ * step of each candidate.  It keeps the fastest (written to *chosen,
+ * nullable, and to the context's seg_rows) and restores the state, clock
+ * and tallies, so the call does not advance the simulation; results of later
+ * steps do not depend on the choice (bitwise).  Needs the fused kernel
+ * (SWE_ERR_UNSUPPORTED otherwise) and a set state (SWE_ERR_STATE); allocates
+ * three state planes for the duration of the call. */
+int32_t swe_autotune_candidates(swe_ctx* ctx, int32_t* rows, int32_t cap);
+swe_status swe_autotune(swe_ctx* ctx, int32_t probe_steps, const int32_t* rows, int32_t nrows, double* ms_per_step,
+                        int32_t* chosen);
+
 /* ---------------------------------------------------------------- batches
  * Many independent scenarios of uneven grid size advanced together (FP32),
  * each with its own CFL step: one persistent cooperative launch per
@@ -205,6 +224,14 @@ swe_status swe_batch_set_bed(swe_batch* b, int32_t idx, const double* z);
 swe_status swe_batch_set_state(swe_batch* b, int32_t idx, const double* eta, const double* u, const double* v);
 swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos);
 swe_status swe_batch_get_state(swe_batch* b, int32_t idx, double* eta, double* u, double* v);
+/* Work-item autotuner of the batched step, as swe_autotune: the built-in
+ * candidates are 16 to 192 rows per item; the probes run on the batch's
+ * current states, which are restored with their clocks and tallies (the
+ * dry-skip flags are cleared).  The items are rebuilt for the chosen height,
+ * which also becomes the batch's seg_rows. */
+int32_t swe_batch_autotune_candidates(swe_batch* b, int32_t* rows, int32_t cap);
+swe_status swe_batch_autotune(swe_batch* b, int32_t probe_steps, const int32_t* rows, int32_t nrows,
+                              double* ms_per_step, int32_t* chosen);
 void swe_batch_destroy(swe_batch* b);
 const char* swe_batch_last_error(const swe_batch* b);
 

@@ -159,12 +159,13 @@ template <class T, int SX, int SY>
 __global__ void __launch_bounds__(256) k_adj_corr(GridK<T> G, StepK<T> S, const T* __restrict__ z,
                                                   const T* __restrict__ n2, Planes3<T> qn, Planes3<T> qs,
                                                   Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX, Planes3<T> GY,
-                                                  Planes3<T> Bc, T* __restrict__ ggn2) {
+                                                  Planes3<T> Bc, T* __restrict__ ggn2, unsigned* dry) {
     constexpr int CX = -SX, CY = -SY;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const size_t k = (size_t)j * G.pitch + i;
     const Cell<T> cs = cell_at(qs.e, qs.u, qs.v, z, k);
+    if (!(cs.e - cs.z > G.h_dry)) atomicOr(dry, 1u);  // outside the differentiated regime
     const bool gx = !(i + CX >= 0 && i + CX < G.nx), gy = !(j + CY >= 0 && j + CY < G.ny);
     const int sidex = CX > 0 ? SIDE_E : SIDE_W, sidey = CY > 0 ? SIDE_N : SIDE_S;
     const Cell<T> xs = gx ? ghost(cs, sidex, G) : cell_at(qs.e, qs.u, qs.v, z, (size_t)((ptrdiff_t)k + CX));
@@ -190,7 +191,7 @@ template <class T, int SX, int SY>
 __global__ void __launch_bounds__(256) k_adj_pred(GridK<T> G, StepK<T> S, const T* __restrict__ z,
                                                   const T* __restrict__ n2, Planes3<T> qn, Planes3<T> Sc,
                                                   Planes3<T> GX, Planes3<T> GY, Planes3<T> Bc, Planes3<T> Pc,
-                                                  Planes3<T> PX, Planes3<T> PY, T* __restrict__ ggn2) {
+                                                  Planes3<T> PX, Planes3<T> PY, T* __restrict__ ggn2, unsigned* dry) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const size_t k = (size_t)j * G.pitch + i;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(256) k_adj_pred(GridK<T> G, StepK<T> S, const 
         ls_e += GY.e[m]; ls_u += GY.u[m]; ls_v += GY.v[m];
     }
     const Cell<T> c = cell_at(qn.e, qn.u, qn.v, z, k);
+    if (!(c.e - c.z > G.h_dry)) atomicOr(dry, 1u);
     const bool gx = !(i + SX >= 0 && i + SX < G.nx), gy = !(j + SY >= 0 && j + SY < G.ny);
     const int sidex = SX > 0 ? SIDE_E : SIDE_W, sidey = SY > 0 ? SIDE_N : SIDE_S;
     const Cell<T> xn = gx ? ghost(c, sidex, G) : cell_at(qn.e, qn.u, qn.v, z, (size_t)((ptrdiff_t)k + SX));
@@ -259,6 +261,15 @@ __global__ void k_gauge_add(T* le, const long long* gidx, int ng, int nx, int pi
         const long long q = gidx[g];
         le[(size_t)(q / nx) * pitch + (size_t)(q % nx)] += (T)res[g];
     }
+}
+
+// Flags a level that has a cell at or below the wet threshold.
+template <class T>
+__global__ void k_wet_check(const T* e, const T* z, int nx, int ny, int pitch, T h_dry, unsigned* dry) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const size_t k = (size_t)j * pitch + i;
+    if (!(e[k] - z[k] > h_dry)) atomicOr(dry, 1u);
 }
 
 template <class T>
@@ -321,62 +332,104 @@ GridK<T> grid_k(const swe_ctx* c) {
 
 // One plain step on given buffers with a frozen step size (device pointer).
 template <class T, int SX, int SY>
-void plain_step_raw(const swe_ctx* c, const GridK<T>& G, DevCtl* ctl, const double* dtp, double* dth,
-                    Planes3<T> in, Planes3<T> ps, Planes3<T> out) {
+void plain_step_raw(const swe_ctx* c, const GridK<T>& G, DevCtl* ctl, const double* dtp, Planes3<T> in,
+                    Planes3<T> ps, Planes3<T> out) {
     const swe_params& p = c->p;
-    k_plain_dt<<<1, 1, 0, c->stream>>>(ctl, 0, 1, dtp, 0, dth, p.cfl, p.dt_max);
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const double area = p.dx * p.dy;
-    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, ctl, p.dx, p.dy, p.g, in.e, in.u, in.v, (const T*)c->z,
+    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, in.e, in.u, in.v, (const T*)c->z,
                                                         (const T*)c->n2, ps.e, ps.u, ps.v, ctl, area);
-    k_plain_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, ctl, p.dx, p.dy, p.g, in.e, in.u, in.v, (const T*)c->z,
-                                                        (const T*)c->n2, ps.e, ps.u, ps.v, out.e, out.u, out.v, 1,
-                                                        area);
+    k_plain_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, ctl, dtp, p.dx, p.dy, p.g, in.e, in.u, in.v,
+                                                        (const T*)c->z, (const T*)c->n2, ps.e, ps.u, ps.v, out.e,
+                                                        out.u, out.v, 1, area);
 }
 
 template <class T, int SX, int SY>
-void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, const double* dtp, double* dth,
-                  Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX, Planes3<T> GY,
-                  Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2) {
+void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, const double* dtp, Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX, Planes3<T> GY,
+                  Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2, unsigned* dry) {
     const swe_params& p = c->p;
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const StepK<T> S = make_stepk<T>(dt, p.dx, p.dy, p.g);
     // 1. the predicted state of this level
-    k_plain_dt<<<1, 1, 0, c->stream>>>(ctl, 0, 1, dtp, 0, dth, p.cfl, p.dt_max);
-    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, ctl, p.dx, p.dy, p.g, qn.e, qn.u, qn.v, (const T*)c->z,
+    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, qn.e, qn.u, qn.v, (const T*)c->z,
                                                         (const T*)c->n2, qs.e, qs.u, qs.v, ctl, p.dx * p.dy);
     // 2-4. corrector VJP, gather + predictor VJP, gather
     k_adj_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, S, (const T*)c->z, (const T*)c->n2, qn, qs, lam, Sc, GX,
-                                                      GY, Bc, ggn2);
+                                                      GY, Bc, ggn2, dry);
     k_adj_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, S, (const T*)c->z, (const T*)c->n2, qn, Sc, GX, GY, Bc, Pc,
-                                                      PX, PY, ggn2);
+                                                      PX, PY, ggn2, dry);
     k_adj_gather<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, Pc, PX, PY, lam);
 }
 
 template <class T>
-void dispatch_plain(const swe_ctx* c, const GridK<T>& G, long long k, DevCtl* ctl, const double* dtp, double* dth,
+void dispatch_plain(const swe_ctx* c, const GridK<T>& G, long long k, DevCtl* ctl, const double* dtp,
                     Planes3<T> in, Planes3<T> ps, Planes3<T> out) {
     int sx, sy;
     step_dirs(c->p.dir_cycle, k, &sx, &sy);
-    if (sx > 0 && sy > 0) plain_step_raw<T, 1, 1>(c, G, ctl, dtp, dth, in, ps, out);
-    else if (sx > 0) plain_step_raw<T, 1, -1>(c, G, ctl, dtp, dth, in, ps, out);
-    else if (sy > 0) plain_step_raw<T, -1, 1>(c, G, ctl, dtp, dth, in, ps, out);
-    else plain_step_raw<T, -1, -1>(c, G, ctl, dtp, dth, in, ps, out);
+    if (sx > 0 && sy > 0) plain_step_raw<T, 1, 1>(c, G, ctl, dtp, in, ps, out);
+    else if (sx > 0) plain_step_raw<T, 1, -1>(c, G, ctl, dtp, in, ps, out);
+    else if (sy > 0) plain_step_raw<T, -1, 1>(c, G, ctl, dtp, in, ps, out);
+    else plain_step_raw<T, -1, -1>(c, G, ctl, dtp, in, ps, out);
 }
 
 template <class T>
 void dispatch_adj(const swe_ctx* c, const GridK<T>& G, long long k, double dt, DevCtl* ctl, const double* dtp,
-                  double* dth, Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX,
-                  Planes3<T> GY, Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2) {
+                  Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX,
+                  Planes3<T> GY, Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2,
+                  unsigned* dry) {
     int sx, sy;
     step_dirs(c->p.dir_cycle, k, &sx, &sy);
-#define SWE_ADJ(A_, B_) adj_step_raw<T, A_, B_>(c, G, dt, ctl, dtp, dth, qn, qs, lam, Sc, GX, GY, Bc, Pc, PX, PY, ggn2)
+#define SWE_ADJ(A_, B_) adj_step_raw<T, A_, B_>(c, G, dt, ctl, dtp, qn, qs, lam, Sc, GX, GY, Bc, Pc, PX, PY, ggn2, dry)
     if (sx > 0 && sy > 0) SWE_ADJ(1, 1);
     else if (sx > 0) SWE_ADJ(1, -1);
     else if (sy > 0) SWE_ADJ(-1, 1);
     else SWE_ADJ(-1, -1);
 #undef SWE_ADJ
 }
+
+// Runs the work `enqueue` puts on the context's stream, captured as a CUDA
+// graph: segments of the same shape re-use one executable graph (updated in
+// place), so a segment costs one launch instead of one per kernel.  When the
+// stream cannot be captured the work is enqueued directly and graphs stay off
+// for the rest of the call.  `enqueue` must be repeatable: it is called again
+// when a capture fails.
+struct SegGraph {
+    cudaStream_t st;
+    bool on;
+    cudaGraphExec_t exec = nullptr;
+    SegGraph(cudaStream_t s, bool use) : st(s), on(use) {}
+    ~SegGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    template <class F>
+    cudaError_t run(F&& enqueue) {
+        if (on) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                enqueue();
+                const cudaError_t le = cudaGetLastError();
+                e = cudaStreamEndCapture(st, &g);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess && exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(exec);
+                    exec = nullptr;
+                }
+            }
+            if (e == cudaSuccess && !exec) e = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) return cudaGraphLaunch(exec, st);
+            cudaGetLastError();  // capture unavailable: direct launches from here on
+            on = false;
+        }
+        enqueue();
+        return cudaGetLastError();
+    }
+};
 
 template <class T>
 swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const double* obs, int kcp, double* loss,
@@ -402,19 +455,21 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
     T* ggn2 = nullptr;
     ACK(buf.get(&ggn2, plane * sizeof(T)));
     long long* gd = nullptr;
-    double *gv = nullptr, *res = nullptr, *dtd = nullptr, *dth = nullptr;
+    double *gv = nullptr, *res = nullptr, *dtd = nullptr;
     DevCtl* ctl = nullptr;
+    unsigned* dry = nullptr;
+    ACK(buf.get(&dry, sizeof(unsigned)));
     ACK(buf.get(&gd, (ng > 0 ? ng : 1) * sizeof(long long)));
     ACK(buf.get(&gv, (size_t)(T_ > 0 ? T_ : 1) * (ng > 0 ? ng : 1) * sizeof(double)));
     ACK(buf.get(&res, (size_t)(T_ > 0 ? T_ : 1) * (ng > 0 ? ng : 1) * sizeof(double)));
     ACK(buf.get(&dtd, (size_t)(T_ > 0 ? T_ : 1) * sizeof(double)));
-    ACK(buf.get(&dth, sizeof(double)));
     ACK(buf.get(&ctl, sizeof(DevCtl)));
     if (ng > 0) ACK(cudaMemcpyAsync(gd, gauges, ng * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
 
     // ---- forward: the library's own step, checkpoints every K steps, gauge series
     std::vector<double> dts(T_ > 0 ? T_ : 1);
     const long long step0 = c->step;
+    SegGraph fgraph(c->stream, c->p.use_graph != 0), rgraph(c->stream, c->p.use_graph != 0);
     if (T_ > 0) {
         if (c->dt_hist_cap < T_) {
             if (c->dt_hist) cudaFree(c->dt_hist);
@@ -424,19 +479,40 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
         }
         c->dt_fixed_cap = 0;
         ACK(swe_launch_call_begin(c));
-        for (int s = 0; s < T_; ++s) {
-            if (s % K == 0) {
-                const Planes3<T>& d = cp[s / K];
-                ACK(cudaMemcpyAsync(d.e, c->eta[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-                ACK(cudaMemcpyAsync(d.u, c->u[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-                ACK(cudaMemcpyAsync(d.v, c->v[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+        // segment by segment: its checkpoint, then its steps with the gauge reads
+        const int cur0 = c->cur;
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int s0 = sg * K, s1 = (s0 + K < T_) ? s0 + K : T_;
+            cudaError_t le = cudaSuccess;
+            auto enqueue = [&]() {
+                le = cudaSuccess;
+                c->cur = (cur0 + s0) & 1;
+                const Planes3<T>& d = cp[sg];
+                cudaMemcpyAsync(d.e, c->eta[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemcpyAsync(d.u, c->u[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemcpyAsync(d.v, c->v[c->cur], plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+                for (int s = s0; s < s1 && le == cudaSuccess; ++s) {
+                    le = c->p.kernel == SWE_KERNEL_FUSED ? swe_launch_fused_step(c, s, step0 + s)
+                                                         : swe_launch_plain_step(c, s, step0 + s);
+                    c->cur = 1 - c->cur;
+                    if (ng > 0)
+                        k_gauge_read<T><<<(ng + 127) / 128, 128, 0, c->stream>>>((const T*)c->eta[c->cur], gd, ng,
+                                                                                  p.nx, c->pitch, gv + (size_t)s * ng);
+                }
+            };
+            // the first segment runs uncaptured: it makes the kernels' first launches
+            if (sg == 0) {
+                enqueue();
+                ACK(le);
+            } else {
+                ACK(fgraph.run(enqueue));
+                ACK(le);
             }
-            if (c->p.kernel == SWE_KERNEL_FUSED) ACK(swe_launch_fused_step(c, s, step0 + s));
-            else ACK(swe_launch_plain_step(c, s, step0 + s));
-            c->cur = 1 - c->cur;
-            if (ng > 0)
-                k_gauge_read<T><<<(ng + 127) / 128, 128, 0, c->stream>>>((const T*)c->eta[c->cur], gd, ng, p.nx,
-                                                                          c->pitch, gv + (size_t)s * ng);
+        }
+        {  // the final level must be wet too
+            dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
+            k_wet_check<T><<<grd, blk, 0, c->stream>>>((const T*)c->eta[c->cur], (const T*)c->z, p.nx, p.ny, c->pitch,
+                                                        (T)p.h_dry, dry);
         }
         ACK(cudaGetLastError());
         c->step += T_;
@@ -466,21 +542,35 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
     if (T_ > 0 && ng > 0) k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(T_ - 1) * ng);
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int s0 = sg * K, s1 = (s0 + K < T_) ? s0 + K : T_;
-        // levels s0 .. s1-1 of this segment, recomputed from its checkpoint
-        ACK(cudaMemcpyAsync(seg[0].e, cp[sg].e, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-        ACK(cudaMemcpyAsync(seg[0].u, cp[sg].u, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-        ACK(cudaMemcpyAsync(seg[0].v, cp[sg].v, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-        for (int s = s0; s + 1 < s1; ++s)
-            dispatch_plain<T>(c, G, step0 + s, ctl, dtd + s, dth, seg[s - s0], qs, seg[s - s0 + 1]);
-        for (int s = s1 - 1; s >= s0; --s) {
-            dispatch_adj<T>(c, G, step0 + s, dts[s], ctl, dtd + s, dth, seg[s - s0], qs, lam, Sc, GX, GY, Bc, Pc, PX,
-                            PY, ggn2);
-            if (s >= 1 && ng > 0)
-                k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(s - 1) * ng);
+        auto enqueue = [&]() {
+            // levels s0 .. s1-1 of this segment, recomputed from its checkpoint
+            cudaMemcpyAsync(seg[0].e, cp[sg].e, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(seg[0].u, cp[sg].u, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(seg[0].v, cp[sg].v, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+            for (int s = s0; s + 1 < s1; ++s)
+                dispatch_plain<T>(c, G, step0 + s, ctl, dtd + s, seg[s - s0], qs, seg[s - s0 + 1]);
+            for (int s = s1 - 1; s >= s0; --s) {
+                dispatch_adj<T>(c, G, step0 + s, dts[s], ctl, dtd + s, seg[s - s0], qs, lam, Sc, GX, GY, Bc, Pc, PX,
+                                PY, ggn2, dry);
+                if (s >= 1 && ng > 0)
+                    k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(s - 1) * ng);
+            }
+        };
+        // the first segment handled (the last in time) runs uncaptured: first launches
+        if (sg == nseg - 1) {
+            enqueue();
+            ACK(cudaGetLastError());
+        } else {
+            ACK(rgraph.run(enqueue));
         }
-        ACK(cudaGetLastError());
     }
     // ---- outputs: d/d eta0, and d/dn = d/d(g n^2) * 2 g n
+    unsigned hdry = 0;
+    ACK(cudaMemcpyAsync(&hdry, dry, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    ACK(cudaStreamSynchronize(c->stream));
+    if (hdry)
+        return afail(c, SWE_ERR_UNSUPPORTED,
+                     "a cell was at or below the wet threshold during the run: the adjoint covers the fully wet regime");
     std::vector<T> hb(plane), hg(plane), hn(plane);
     ACK(cudaMemcpyAsync(hb.data(), lam.e, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
     ACK(cudaMemcpyAsync(hg.data(), ggn2, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));

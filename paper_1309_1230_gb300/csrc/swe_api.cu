@@ -3,6 +3,7 @@
 // context's stream.  No step arithmetic lives here.
 #include <cmath>
 #include <cstdarg>
+#include <vector>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -169,7 +170,7 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
         free_all(c, [](void* q) { if (q) cudaFree(q); });
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         if (c->h_ctl) cudaFreeHost(c->h_ctl);
-        free(c->tmaps);
+        swe_fused_release(c);
         delete c;
         return SWE_ERR_CUDA;
     };
@@ -227,7 +228,7 @@ void swe_destroy(swe_ctx* c) {
     free_all(c, [](void* q) { if (q) cudaFree(q); });
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-    free(c->tmaps);  // host-side work plan
+    swe_fused_release(c);  // work plan
     delete c;
 }
 
@@ -430,6 +431,103 @@ swe_status swe_step(swe_ctx* c, int32_t nsteps, const double* dt_fixed, double* 
     if (c->h_ctl->flags & SWE_FLAG_TIMEOUT) return fail(c, SWE_ERR_TIMEOUT, "a device-side wait gave up");
     if ((c->h_ctl->flags & SWE_FLAG_NONFINITE) || (info && (info->flags & SWE_FLAG_NONFINITE)))
         return fail(c, SWE_ERR_NONFINITE, "non-finite value in the state");
+    return SWE_OK;
+}
+
+int32_t swe_autotune_candidates(swe_ctx* c, int32_t* rows, int32_t cap) {
+    swe_status s = check_ctx(c);
+    if (s != SWE_OK) return -(int32_t)s;
+    if (c->p.kernel != SWE_KERNEL_FUSED)
+        return -(int32_t)fail(c, SWE_ERR_UNSUPPORTED, "only the fused step has a work-item shape to tune");
+    if (!rows || cap < 1) return -(int32_t)fail(c, SWE_ERR_ARG, "rows is NULL or cap < 1");
+    return swe_fused_row_candidates(c, rows, cap);
+}
+
+swe_status swe_autotune(swe_ctx* c, int32_t probe_steps, const int32_t* rows, int32_t nrows, double* ms_per_step,
+                        int32_t* chosen) {
+    swe_status s = check_ctx(c);
+    if (s != SWE_OK) return s;
+    if (!c->state_set) return fail(c, SWE_ERR_STATE, "swe_set_state must come first");
+    if (c->p.kernel != SWE_KERNEL_FUSED) return fail(c, SWE_ERR_UNSUPPORTED, "only the fused step has a work-item shape to tune");
+    if (probe_steps < 1 || probe_steps > 10000) return fail(c, SWE_ERR_ARG, "probe_steps must lie in [1, 10000]");
+    std::vector<int> cand;
+    if (rows) {
+        if (nrows < 1) return fail(c, SWE_ERR_ARG, "nrows < 1");
+        for (int i = 0; i < nrows; ++i) {
+            if (rows[i] < 1 || rows[i] > 4096) return fail(c, SWE_ERR_ARG, "rows[%d] must lie in [1, 4096]", i);
+            cand.push_back(rows[i]);
+        }
+    } else {
+        if (ms_per_step) return fail(c, SWE_ERR_ARG, "ms_per_step needs the candidate list");
+        int tmp[16];
+        const int n = swe_fused_row_candidates(c, tmp, 16);
+        cand.assign(tmp, tmp + n);
+    }
+    if ((s = ensure_hist(c, probe_steps)) != SWE_OK) return s;
+    c->dt_fixed_cap = 0;
+    // the state, clock and tallies to come back to after every probe
+    const int cur0 = c->cur;
+    const long long step0 = c->step;
+    const size_t bytes = c->plane * (size_t)c->real_size;
+    DevCtl saved;
+    CK(c, cudaMemcpyAsync(&saved, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    struct Scratch {
+        void* p[3] = {nullptr, nullptr, nullptr};
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Scratch() {
+            for (void* q : p)
+                if (q) cudaFree(q);
+            for (cudaEvent_t q : e)
+                if (q) cudaEventDestroy(q);
+        }
+    } k;
+    void* live[3] = {c->eta[cur0], c->u[cur0], c->v[cur0]};
+    for (int f = 0; f < 3; ++f) {
+        CK(c, cudaMalloc(&k.p[f], bytes));
+        CK(c, cudaMemcpyAsync(k.p[f], live[f], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(c, cudaEventCreate(&k.e[0]));
+    CK(c, cudaEventCreate(&k.e[1]));
+    auto restore = [&]() -> cudaError_t {
+        c->cur = cur0;
+        c->step = step0;
+        cudaError_t e = cudaSuccess;
+        for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+            e = cudaMemcpyAsync(live[f], k.p[f], bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &saved, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream);
+        return e;
+    };
+    int best = -1;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        c->p.seg_rows = cand[i];
+        CK(c, swe_fused_prepare(c));
+        CK(c, restore());
+        CK(c, swe_launch_call_begin(c));
+        CK(c, swe_fused_run(c, 1));  // warm-up
+        c->step += 1;
+        CK(c, cudaEventRecord(k.e[0], c->stream));
+        CK(c, swe_fused_run(c, probe_steps));
+        CK(c, cudaEventRecord(k.e[1], c->stream));
+        CK(c, cudaEventSynchronize(k.e[1]));
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, k.e[0], k.e[1]));
+        ms /= (float)probe_steps;
+        if (ms_per_step) ms_per_step[i] = ms;
+        if (best < 0 || ms < best_ms) { best = (int)i; best_ms = ms; }
+        unsigned flags = 0;
+        CK(c, cudaMemcpy(&flags, &c->ctl->flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (flags & SWE_FLAG_TIMEOUT) {
+            c->p.seg_rows = 0;
+            return fail(c, SWE_ERR_TIMEOUT, "a device-side wait gave up while probing %d rows", cand[i]);
+        }
+    }
+    c->p.seg_rows = cand[best];
+    CK(c, swe_fused_prepare(c));
+    CK(c, restore());
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (chosen) *chosen = cand[best];
     return SWE_OK;
 }
 

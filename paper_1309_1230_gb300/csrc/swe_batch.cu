@@ -462,6 +462,52 @@ swe_status check_batch(swe_batch* b) {
     return SWE_OK;
 }
 
+// (Re)builds the work items for L rows per item: the per-scenario table, the
+// claim order (scenarios by decreasing size, so the largest are claimed
+// first; the flags stay indexed scenario-major) and cleared dry-skip flags.
+cudaError_t build_items(swe_batch* b, int L) {
+    const int count = b->count;
+    std::vector<Scen> sc(count);
+    std::vector<BItem> items;
+    for (int s = 0; s < count; ++s) {
+        sc[s].nx = b->nx[s]; sc[s].ny = b->ny[s]; sc[s].row0 = b->row0[s];
+        sc[s].nxs = (b->nx[s] + Gm::OUT - 1) / Gm::OUT;
+        sc[s].nys = (b->ny[s] + L - 1) / L;
+        sc[s].gn2 = (T)(b->p.g * b->n[s] * b->n[s]);
+    }
+    std::vector<int> item0(count);
+    for (int s = 0; s < count; ++s) {  // item index = item0 + ky * nxs + kx, scenario-major
+        item0[s] = (int)items.size();
+        for (int ky = 0; ky < sc[s].nys; ++ky)
+            for (int kx = 0; kx < sc[s].nxs; ++kx) items.push_back({s, kx, ky, (int)items.size()});
+    }
+    for (int s = 0; s < count; ++s) sc[s].item0 = item0[s];
+    std::vector<BItem> claim;
+    claim.reserve(items.size());
+    for (int s : b->order)
+        for (int q = 0; q < sc[s].nxs * sc[s].nys; ++q) claim.push_back(items[item0[s] + q]);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return e;
+    void* old[3] = {b->scen, b->items, b->flags};
+    for (void* q : old)
+        if (q && (e = cudaFree(q)) != cudaSuccess) return e;
+    b->scen = nullptr; b->items = nullptr; b->flags = nullptr;
+    b->nitems = (int)items.size();
+    b->L = L;
+    if ((e = cudaMalloc(&b->scen, count * sizeof(Scen))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(b->scen, sc.data(), count * sizeof(Scen), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&b->items, b->nitems * sizeof(BItem))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(b->items, claim.data(), b->nitems * sizeof(BItem), cudaMemcpyHostToDevice, b->stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&b->flags, 2 * (size_t)b->nitems * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->flags, 0, 2 * (size_t)b->nitems * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }  // captured the old item count
+    b->graph_steps = -1;
+    return cudaStreamSynchronize(b->stream);
+}
+
 int occupancy_batch(bool kappa) {
     int nb = 0;
     const int smem = Gm::WARP_SMEM;
@@ -531,39 +577,11 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
         }
     if ((e = cudaMalloc(&b->z, b->plane * sizeof(T))) != cudaSuccess) return bail("bed", e);
     if ((e = cudaMemset(b->z, 0, b->plane * sizeof(T))) != cudaSuccess) return bail("memset", e);
-    // items: scenarios by decreasing size, so the largest are claimed first
     b->order.resize(count);
-    for (int s = 0; s < count; ++s) b->order[s] = s;
+    for (int q = 0; q < count; ++q) b->order[q] = q;
     std::stable_sort(b->order.begin(), b->order.end(),
                      [&](int a, int c) { return (long long)nx[a] * ny[a] > (long long)nx[c] * ny[c]; });
-    std::vector<Scen> sc(count);
-    std::vector<BItem> items;
-    for (int s = 0; s < count; ++s) {
-        sc[s].nx = nx[s]; sc[s].ny = ny[s]; sc[s].row0 = b->row0[s];
-        sc[s].nxs = (nx[s] + Gm::OUT - 1) / Gm::OUT;
-        sc[s].nys = (ny[s] + b->L - 1) / b->L;
-        sc[s].gn2 = (T)(p->g * manning_n[s] * manning_n[s]);
-    }
-    std::vector<int> item0(count);
-    for (int s = 0; s < count; ++s) {  // item index = item0 + ky * nxs + kx, scenario-major
-        item0[s] = (int)items.size();
-        for (int ky = 0; ky < sc[s].nys; ++ky)
-            for (int kx = 0; kx < sc[s].nxs; ++kx) items.push_back({s, kx, ky, (int)items.size()});
-    }
-    for (int s = 0; s < count; ++s) sc[s].item0 = item0[s];
-    // claim order: largest scenarios first (the flags stay indexed scenario-major)
-    std::vector<BItem> claim;
-    claim.reserve(items.size());
-    for (int s : b->order)
-        for (int q = 0; q < sc[s].nxs * sc[s].nys; ++q) claim.push_back(items[item0[s] + q]);
-    b->nitems = (int)items.size();
-    if ((e = cudaMalloc(&b->scen, count * sizeof(Scen))) != cudaSuccess) return bail("scen", e);
-    if ((e = cudaMemcpy(b->scen, sc.data(), count * sizeof(Scen), cudaMemcpyHostToDevice)) != cudaSuccess) return bail("scen", e);
-    if ((e = cudaMalloc(&b->items, b->nitems * sizeof(BItem))) != cudaSuccess) return bail("items", e);
-    if ((e = cudaMemcpy(b->items, claim.data(), b->nitems * sizeof(BItem), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail("items", e);
-    if ((e = cudaMalloc(&b->flags, 2 * (size_t)b->nitems * sizeof(unsigned))) != cudaSuccess) return bail("flags", e);
-    if ((e = cudaMemset(b->flags, 0, 2 * (size_t)b->nitems * sizeof(unsigned))) != cudaSuccess) return bail("flags", e);
+    if ((e = build_items(b, b->L)) != cudaSuccess) return bail("work items", e);
     if ((e = cudaMalloc(&b->counters, 3 * sizeof(unsigned))) != cudaSuccess) return bail("counters", e);
     if ((e = cudaMemset(b->counters, 0, 3 * sizeof(unsigned))) != cudaSuccess) return bail("counters", e);
     if ((e = cudaMalloc(&b->bar, 2 * sizeof(unsigned))) != cudaSuccess) return bail("bar", e);
@@ -649,6 +667,41 @@ swe_status swe_batch_set_state(swe_batch* b, int32_t idx, const double* eta, con
     return SWE_OK;
 }
 
+// Queues nsteps steps: one persistent cooperative launch, captured in a graph
+// when `graph` is set (re-captured when the step count, starting step or
+// buffer parity changes).
+static cudaError_t launch_steps(swe_batch* b, int nsteps, bool graph) {
+    BatchArgs B = make_args(b, nsteps);
+    const bool kap = b->p.kappa != 0.0;
+    void* kern = kap ? (void*)k_batch<true> : (void*)k_batch<false>;
+    const CUtensorMap* A = b->tm[0];
+    const CUtensorMap* Bm = b->tm[1];
+    void* args[] = {(void*)&A[0], (void*)&A[1], (void*)&A[2], (void*)&Bm[0], (void*)&Bm[1], (void*)&Bm[2],
+                    (void*)&b->tmz, (void*)&B};
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->counters, 0, 3 * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
+    if (!graph) return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream);
+    if (!b->graph || b->graph_steps != nsteps || b->graph_k != b->step || b->graph_cur != b->cur) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        const cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream);
+        const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return le != cudaSuccess ? le : ce;
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        b->graph_steps = nsteps;
+        b->graph_k = b->step;
+        b->graph_cur = b->cur;
+    }
+    return cudaGraphLaunch(b->graph, b->stream);
+}
+
 static swe_status prologue(swe_batch* b) {
     BatchArgs B = make_args(b, 0);
     BCK(b, cudaMemsetAsync(b->flags, 0, 2 * (size_t)b->nitems * sizeof(unsigned), b->stream));
@@ -670,39 +723,7 @@ swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos) {
     }
     k_batch_begin<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
     BCK(b, cudaGetLastError());
-    if (nsteps > 0) {
-        BatchArgs B = make_args(b, nsteps);
-        const bool kap = b->p.kappa != 0.0;
-        void* kern = kap ? (void*)k_batch<true> : (void*)k_batch<false>;
-        const CUtensorMap* A = b->tm[0];
-        const CUtensorMap* Bm = b->tm[1];
-        void* args[] = {(void*)&A[0], (void*)&A[1], (void*)&A[2], (void*)&Bm[0], (void*)&Bm[1], (void*)&Bm[2],
-                        (void*)&b->tmz, (void*)&B};
-        BCK(b, cudaMemsetAsync(b->counters, 0, 3 * sizeof(unsigned), b->stream));
-        BCK(b, cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream));
-        if (b->p.use_graph) {
-            // one persistent cooperative launch captured in a graph (re-captured when
-            // the step count, starting step or buffer parity changes)
-            if (!b->graph || b->graph_steps != nsteps || b->graph_k != b->step || b->graph_cur != b->cur) {
-                if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
-                cudaGraph_t g = nullptr;
-                BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream);
-                cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
-                BCK(b, le);
-                BCK(b, ce);
-                cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
-                cudaGraphDestroy(g);
-                BCK(b, ie);
-                b->graph_steps = nsteps;
-                b->graph_k = b->step;
-                b->graph_cur = b->cur;
-            }
-            BCK(b, cudaGraphLaunch(b->graph, b->stream));
-        } else {
-            BCK(b, cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream));
-        }
-    }
+    if (nsteps > 0) BCK(b, launch_steps(b, nsteps, b->p.use_graph != 0));
     b->step += nsteps;
     b->cur = (b->cur + nsteps) & 1;
     BCK(b, cudaMemcpyAsync(b->h_ctl, b->ctl, b->count * sizeof(DevCtl), cudaMemcpyDeviceToHost, b->stream));
@@ -748,6 +769,105 @@ swe_status swe_batch_get_state(swe_batch* b, int32_t idx, double* eta, double* u
         BCK(b, cudaMemcpyAsync(dst[f], b->stage + f * n, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     }
     BCK(b, cudaStreamSynchronize(b->stream));
+    return SWE_OK;
+}
+
+// Built-in candidate rows per item of the batched step.
+static const int kBatchRows[] = {16, 24, 32, 48, 64, 96, 128, 192};
+
+int32_t swe_batch_autotune_candidates(swe_batch* b, int32_t* rows, int32_t cap) {
+    swe_status s = check_batch(b);
+    if (s != SWE_OK) return -(int32_t)s;
+    if (!rows || cap < 1) return -(int32_t)bfail(b, SWE_ERR_ARG, "rows is NULL or cap < 1");
+    const int n = (int)(sizeof(kBatchRows) / sizeof(kBatchRows[0]));
+    for (int i = 0; i < n && i < cap; ++i) rows[i] = kBatchRows[i];
+    return n < cap ? n : cap;
+}
+
+swe_status swe_batch_autotune(swe_batch* b, int32_t probe_steps, const int32_t* rows, int32_t nrows,
+                              double* ms_per_step, int32_t* chosen) {
+    swe_status s = check_batch(b);
+    if (s != SWE_OK) return s;
+    if (probe_steps < 1 || probe_steps > 10000) return bfail(b, SWE_ERR_ARG, "probe_steps must lie in [1, 10000]");
+    for (int q = 0; q < b->count; ++q)
+        if (!b->state_set[q]) return bfail(b, SWE_ERR_STATE, "scenario %d has no state", q);
+    std::vector<int> cand;
+    if (rows) {
+        if (nrows < 1) return bfail(b, SWE_ERR_ARG, "nrows < 1");
+        for (int i = 0; i < nrows; ++i) {
+            if (rows[i] < 1 || rows[i] > 4096) return bfail(b, SWE_ERR_ARG, "rows[%d] must lie in [1, 4096]", i);
+            cand.push_back(rows[i]);
+        }
+    } else {
+        if (ms_per_step) return bfail(b, SWE_ERR_ARG, "ms_per_step needs the candidate list");
+        cand.assign(std::begin(kBatchRows), std::end(kBatchRows));
+    }
+    if (b->need_prologue) {
+        if ((s = prologue(b)) != SWE_OK) return s;
+        b->need_prologue = false;
+    }
+    // the state, clocks and tallies to come back to after every probe
+    const int cur0 = b->cur;
+    const long long step0 = b->step;
+    std::vector<DevCtl> saved(b->count);
+    BCK(b, cudaMemcpyAsync(saved.data(), b->ctl, b->count * sizeof(DevCtl), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    struct Scratch {
+        T* p[3] = {nullptr, nullptr, nullptr};
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Scratch() {
+            for (T* q : p)
+                if (q) cudaFree(q);
+            for (cudaEvent_t q : e)
+                if (q) cudaEventDestroy(q);
+        }
+    } k;
+    const size_t bytes = b->plane * sizeof(T);
+    for (int f = 0; f < 3; ++f) {
+        BCK(b, cudaMalloc(&k.p[f], bytes));
+        BCK(b, cudaMemcpyAsync(k.p[f], b->pl[cur0][f], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    BCK(b, cudaEventCreate(&k.e[0]));
+    BCK(b, cudaEventCreate(&k.e[1]));
+    auto restore = [&]() -> swe_status {
+        b->cur = cur0;
+        b->step = step0;
+        for (int f = 0; f < 3; ++f)
+            BCK(b, cudaMemcpyAsync(b->pl[cur0][f], k.p[f], bytes, cudaMemcpyDeviceToDevice, b->stream));
+        BCK(b, cudaMemcpyAsync(b->ctl, saved.data(), b->count * sizeof(DevCtl), cudaMemcpyHostToDevice, b->stream));
+        // cleared flags: the first steps after this compute every item
+        BCK(b, cudaMemsetAsync(b->flags, 0, 2 * (size_t)b->nitems * sizeof(unsigned), b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        return SWE_OK;
+    };
+    int best = -1;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        BCK(b, build_items(b, cand[i]));
+        if ((s = restore()) != SWE_OK) return s;
+        k_batch_begin<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
+        BCK(b, cudaGetLastError());
+        BCK(b, launch_steps(b, 1, false));  // warm-up
+        b->step += 1;
+        b->cur ^= 1;
+        BCK(b, cudaEventRecord(k.e[0], b->stream));
+        BCK(b, launch_steps(b, probe_steps, false));
+        BCK(b, cudaEventRecord(k.e[1], b->stream));
+        BCK(b, cudaEventSynchronize(k.e[1]));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, k.e[0], k.e[1]));
+        ms /= (float)probe_steps;
+        if (ms_per_step) ms_per_step[i] = ms;
+        if (best < 0 || ms < best_ms) { best = (int)i; best_ms = ms; }
+        BCK(b, cudaMemcpy(b->h_ctl, b->ctl, b->count * sizeof(DevCtl), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < b->count; ++q)
+            if (b->h_ctl[q].flags & SWE_FLAG_TIMEOUT)
+                return bfail(b, SWE_ERR_TIMEOUT, "a device-side wait gave up while probing %d rows", cand[i]);
+    }
+    BCK(b, build_items(b, cand[best]));
+    if ((s = restore()) != SWE_OK) return s;
+    b->p.seg_rows = cand[best];
+    if (chosen) *chosen = cand[best];
     return SWE_OK;
 }
 

@@ -1,6 +1,8 @@
 // swe_fused.cu -- host side of the fused step: TMA tensor maps of the
-// state planes and the work plan (rows per item chosen so that the items
-// fill whole waves of the resident warps).  The kernel is in swe_fused.cuh.
+// state planes and the work plan (rows per item, items per step, grid).  The
+// kernel is in swe_fused.cuh.
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 
 #include "swe_fused.cuh"
@@ -36,21 +38,19 @@ cudaError_t encode(CUtensorMap* m, const void* base, const swe_ctx* c) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Rows per item chosen so that the items fill whole waves of the resident
-// warps: minimise ceil(items / warps) * (L + 4) over L.
+// Rows per item: the warps take items from a queue, so the items only need
+// to be small enough that the warps finish together (about ITEMS_PER_WARP
+// each) while long enough that the four warm-up rows of an item stay a small
+// share of its work.
+constexpr int ITEMS_PER_WARP = 4;
+
 int choose_rows(int ny, int nxs, int warps, int forced) {
     if (forced > 0) return forced;
-    int best = 64;
-    double best_cost = 1e300;
-    for (int L = 16; L <= 512; L += 4) {
-        int nys = (ny + L - 1) / L;
-        long long items = (long long)nxs * nys;
-        long long rounds = (items + warps - 1) / warps;
-        double cost = (double)rounds * (double)(L + 4);
-        if (cost < best_cost - 1e-9) { best_cost = cost; best = L; }
-        if (L >= ny) break;
-    }
-    return best;
+    const double want = (double)ny * nxs / ((double)ITEMS_PER_WARP * warps);
+    int L = ((int)want + 3) / 4 * 4;
+    if (L < 32) L = 32;
+    if (L > 512) L = 512;
+    return L;
 }
 
 template <class T, int CPT>
@@ -73,6 +73,10 @@ cudaError_t prepare_t(swe_ctx* c, Plan& pl) {
     pl.nys = (c->p.ny + pl.L - 1) / pl.L;
     pl.nitems = pl.nxs * pl.nys;
     if (pl.grid * NWARP > pl.nitems) pl.grid = (pl.nitems + NWARP - 1) / NWARP;
+    if (pl.flags) cudaFree(pl.flags);
+    pl.flags = nullptr;
+    if ((e = cudaMalloc(&pl.flags, 2 * (size_t)pl.nitems * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(pl.flags, 0, 2 * (size_t)pl.nitems * sizeof(unsigned), c->stream)) != cudaSuccess) return e;
     pl.ready = true;
     return cudaSuccess;
 }
@@ -88,6 +92,47 @@ cudaError_t swe_fused_prepare(swe_ctx* c) {
     Plan& pl = *(Plan*)c->tmaps;
     if (c->real_size == 4) return prepare_t<float, 2>(c, pl);
     return prepare_t<double, 2>(c, pl);
+}
+
+// Candidate rows per item for the autotuner: the heights that give about q
+// items per resident warp for q in {1, 2, 3, 4, 6, 8}, and 32 and 64 rows;
+// multiples of 4 in [16, 512], ascending, no repeats.
+int swe_fused_row_candidates(swe_ctx* c, int* out, int cap) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->p.device);
+    const int per_sm = c->real_size == 4 ? occupancy_f32(c) : occupancy_f64(c);
+    const double warps = (double)sms * per_sm * NWARP;
+    const int nxs = (c->p.nx + Geo<float, 2>::OUT - 1) / Geo<float, 2>::OUT;
+    int v[8], n = 0;
+    const int q[6] = {1, 2, 3, 4, 6, 8};
+    for (int i = 0; i < 6; ++i) {
+        int L = ((int)std::ceil((double)c->p.ny * nxs / (q[i] * warps)) + 3) / 4 * 4;
+        v[n++] = L < 16 ? 16 : (L > 512 ? 512 : L);
+    }
+    v[n++] = 32;
+    v[n++] = 64;
+    std::sort(v, v + n);
+    const int m = (int)(std::unique(v, v + n) - v);
+    for (int i = 0; i < m && i < cap; ++i) out[i] = v[i];
+    return m < cap ? m : cap;
+}
+
+void swe_fused_release(swe_ctx* c) {
+    if (c->tmaps) {
+        Plan& pl = *(Plan*)c->tmaps;
+        if (pl.flags) cudaFree(pl.flags);
+        free(c->tmaps);
+        c->tmaps = nullptr;
+    }
+}
+
+// Forgets what the dry-skip flags know (the state may have been replaced):
+// the first two steps after this compute every item.
+cudaError_t swe_fused_reset_flags(swe_ctx* c) {
+    if (!c->tmaps) return cudaSuccess;
+    Plan& pl = *(Plan*)c->tmaps;
+    if (!pl.flags) return cudaSuccess;
+    return cudaMemsetAsync(pl.flags, 0, 2 * (size_t)pl.nitems * sizeof(unsigned), c->stream);
 }
 
 cudaError_t swe_launch_fused_step(swe_ctx* c, int s, long long k) {

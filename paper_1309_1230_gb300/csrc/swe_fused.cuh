@@ -6,7 +6,8 @@
 #pragma once
 //
 // Decomposition.  A work item is a column strip of 32*CPT cells (one warp, CPT
-// cells per lane) by a segment of L rows.  Along x the warp outputs 31 of its
+// cells per lane) by a segment of L rows; the resident warps take items from
+// a per-step atomic queue, costliest first, so that they finish together.  Along x the warp outputs 31 of its
 // 32 lanes: the remaining lane (lane 0 when the predictor differences
 // forward, lane 31 when backward) only computes the predicted values its
 // neighbour's corrector needs.  Along y the warp marches row by row; the
@@ -77,7 +78,33 @@ struct Args : ItemIO<T> {
     int s;                         // step within the call
     int slot_cur, slot_next, slot_zero;
     int nxs, nys, L, nitems;
+    int nfull;                     // row bands of the full L rows
+    // dry-item skip (null: off): per item, bit 0 = no wet output cell, bit 1 =
+    // both ping-pong copies of the item agree; written for level k+1 in step k
+    const unsigned* fl_in;
+    unsigned* fl_out;
+    int inflow_mask;               // bit s: side s has an inflow boundary
 };
+
+// Work item of queue position q.  Items are handed out through an atomic
+// counter in order of decreasing cost: the strips at the x boundary (their
+// rows run the boundary code), then the interior strips, then the short last
+// row band.
+__device__ __forceinline__ void item_of(int q, int nxs, int nfull, int& kx, int& ky) {
+    const int ne = nxs >= 2 ? 2 : 1;
+    const int n_edge = ne * nfull, n_full = nxs * nfull;
+    if (q < n_edge) {
+        ky = q / ne;
+        kx = (q - ky * ne) == 0 ? 0 : nxs - 1;
+    } else if (q < n_full) {
+        const int r = q - n_edge, ni = nxs - ne;
+        ky = r / ni;
+        kx = 1 + (r - ky * ni);
+    } else {
+        ky = nfull;
+        kx = q - n_full;
+    }
+}
 
 __device__ __forceinline__ unsigned saddr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -272,7 +299,7 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 // One ring row r (ring index k) of an item: y switch of row r-1, the
 // predictor and x dissipation of row r-1, and the corrector, average,
 // dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.
-template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR>
+template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN>
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
@@ -288,10 +315,13 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     fence_async_smem();  // ring row k-4 (read last iteration) is refilled next
     if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
     if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
-    if (k < 2) return;
+    if (GEN && k < 2) return;
 
-    // -------- level-n rows r, r-1, r-2 (ghost cells outside [0, ny))
-    const bool brow = (r - 2 <= 0) || (r >= ny);
+    // -------- level-n rows r, r-1, r-2 (ghost cells outside [0, ny)).  The
+    // lean instantiation (GEN false) serves interior rows of items away from
+    // the x boundary, where every boundary test below is false.
+    const bool brow = GEN && ((r - 2 <= 0) || (r >= ny));
+    const bool edge = GEN && I.edge;
     const unsigned g = I.g0 + (unsigned)k;
     const unsigned char* s0 = I.ring + ((g) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
     const unsigned char* s1 = I.ring + ((g - 1u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
@@ -362,7 +392,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             if (SX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
             if (SY > 0) { fn[j] = qyn; fs[j] = qy[j]; } else { fn[j] = qy[j]; fs[j] = qyn; }
         }
-        if (I.edge) {
+        if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
                 const int x = I.x0c + j;
@@ -405,7 +435,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             T eo, uo, vo;
             stage<SX, SY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], cc.e, cc.u, cc.v, gn2v[j], S, hd, eo, uo, vo);
             T ad = wetdry_fix(eo, uo, vo, cc.z, hd);
-            if (I.edge && I.x0c + j >= nx) ad = T(0);
+            if (edge && I.x0c + j >= nx) ad = T(0);
             added += ad;
             P.e[j] = eo; P.u[j] = uo; P.v[j] = vo; P.z[j] = cc.z;
             P.qy[j] = (eo - cc.z) * vo;
@@ -426,7 +456,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             T hl[CPT], hr[CPT];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) { hl[j] = L.e[j] - L.z[j]; hr[j] = Rr.e[j] - Rr.z[j]; }
-            if (I.edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
+            if (edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
                     if (I.x0c + j == 0) hl[j] = h1[j];
@@ -453,14 +483,14 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             for (int j = 0; j < CPT; ++j) {
                 const T nur = j + 1 < CPT ? nuc[j + 1 < CPT ? j + 1 : j] : nu_hi;
                 T eps = face_eps(h1[j] > hd, hr[j] > hd, nuc[j], nur);
-                if (I.edge && I.x0c + j + 1 >= nx) eps = T(0);
+                if (edge && I.x0c + j + 1 >= nx) eps = T(0);
                 fr[0][j] = dflux(eps, Rr.e[j], c.e[j]);
                 fr[1][j] = dflux(eps, Rr.u[j], c.u[j]);
                 fr[2][j] = dflux(eps, Rr.v[j], c.v[j]);
             }
             {
                 T eps = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
-                if (I.edge && I.x0c - 1 < 0) eps = T(0);
+                if (edge && I.x0c - 1 < 0) eps = T(0);
                 fl0[0] = dflux(eps, c.e[0], L.e[0]);
                 fl0[1] = dflux(eps, c.u[0], L.u[0]);
                 fl0[2] = dflux(eps, c.v[0], L.v[0]);
@@ -502,7 +532,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             if (CX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
             if (CY > 0) { fn[j] = ys.qy[j]; fs[j] = pc.qy[j]; } else { fn[j] = pc.qy[j]; fs[j] = ys.qy[j]; }
         }
-        if (I.edge) {
+        if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
                 const int x = I.x0c + j;
@@ -559,7 +589,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             T spj = cfl_speed(oe[j], ou[j], ov[j], cc.z, G);
             const T sum = oe[j] + ou[j] + ov[j];
             const bool bj = !((sum - sum) == T(0));
-            if (I.edge && I.x0c + j >= nx) { ad = T(0); spj = T(0); }
+            if (edge && I.x0c + j >= nx) { ad = T(0); spj = T(0); }
             added += ad;
             sp = spj > sp ? spj : sp;
             bad = bad || bj;
@@ -574,7 +604,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             st_vec<T, CPT>(A.u1 + o, ou);
             st_vec<T, CPT>(A.v1 + o, ov);
         }
-        if (I.edge) {
+        if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
                 const T qxn = h2[j] * R2.u[j];
@@ -587,7 +617,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         if (brow && (C == 0 || C == ny - 1)) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                const bool in = st && !(I.edge && I.x0c + j >= nx);
+                const bool in = st && !(edge && I.x0c + j >= nx);
                 const T qyn = h2[j] * R2.v[j];
                 const T sv = T(0.5) * (face_bnd(SIDE_S, qyn, G) + face_bnd(SIDE_S, pc.qy[j], G));
                 const T nv = T(0.5) * (face_bnd(SIDE_N, qyn, G) + face_bnd(SIDE_N, pc.qy[j], G));
@@ -598,17 +628,18 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     };
 
     if (SY > 0) {  // the corrector reads P(C-1) from the buffer the predictor overwrites
-        if (k >= 4) corrector();
+        if (!GEN || k >= 4) corrector();
         predictor();
     } else {       // the corrector reads P(C+1), which the predictor produces
         predictor();
-        if (k >= 4) corrector();
+        if (!GEN || k >= 4) corrector();
     }
     __syncwarp();
 }
 
+// Returns (for the whole warp) whether any output cell of the item is wet.
 template <class T, int CPT, int SX, int SY, bool KAPPA>
-__device__ __forceinline__ void run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
+__device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
                                          Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
                                          const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out) {
     fence_async_smem();  // the previous item's rows were read through the generic proxy
@@ -625,15 +656,23 @@ __device__ __forceinline__ void run_item(const ItemIO<T>& A, const StepK<T>& S, 
     ia.clamp = ia.bw = ia.be = ia.bs = ia.bn = ia.smax = T(0);
     ia.bad = false;
     int k = 0;
+    const int ny = A.G.ny;
 #pragma unroll 1
     for (; k + 1 < I.nr; k += 2) {
-        row_step<T, CPT, SX, SY, KAPPA, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-        if (timed_out) break;
-        row_step<T, CPT, SX, SY, KAPPA, 1>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        const int r = I.y0 - 2 + k;
+        if (!I.edge && k >= 4 && r - 2 > 0 && r + 1 < ny) {
+            row_step<T, CPT, SX, SY, KAPPA, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            if (timed_out) break;
+            row_step<T, CPT, SX, SY, KAPPA, 1, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        } else {
+            row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            if (timed_out) break;
+            row_step<T, CPT, SX, SY, KAPPA, 1, true>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        }
         if (timed_out) break;
     }
     if (!timed_out && k < I.nr) {
-        row_step<T, CPT, SX, SY, KAPPA, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
         ++k;
     }
     if (timed_out) {
@@ -651,6 +690,7 @@ __device__ __forceinline__ void run_item(const ItemIO<T>& A, const StepK<T>& S, 
     acc.bw += (double)ia.bw; acc.be += (double)ia.be; acc.bs += (double)ia.bs; acc.bn += (double)ia.bn;
     acc.smax = fmax(acc.smax, (double)ia.smax);
     acc.bad = acc.bad || ia.bad;
+    return __any_sync(FULL, ia.smax > T(0));
 }
 
 template <class T, int CPT, int SX, int SY, bool KAPPA>
@@ -675,6 +715,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
             c->dt_maxs = fmax(c->dt_maxs, dt);
             A.dt_hist[A.s] = dt;
             c->smax[A.slot_zero] = 0ull;
+            c->qctr[A.slot_zero] = 0u;  // the previous step's queue (all its CTAs have finished)
         }
     }
     if (lane == 0)
@@ -702,9 +743,35 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         for (int j = 0; j < CPT; ++j)
             Cy.P[b].e[j] = Cy.P[b].u[j] = Cy.P[b].v[j] = Cy.P[b].z[j] = Cy.P[b].qy[j] = T(0);
     I.yoff = 0;
-    const int gw = blockIdx.x * NWARP + warp, nw = gridDim.x * NWARP;
-    for (int item = gw; item < A.nitems && !timed_out; item += nw) {
-        const int kx = item % A.nxs, ky = item / A.nxs;
+    // items from the step's queue; the next index is fetched while an item runs
+    unsigned* qc = &A.ctl->qctr[A.slot_cur];
+    int item = 0;
+    if (lane == 0) item = (int)atomicAdd(qc, 1u);
+    item = __shfl_sync(FULL, item, 0);
+    while (item < A.nitems && !timed_out) {
+        int nxt = 0;
+        if (lane == 0) nxt = (int)atomicAdd(qc, 1u);
+        int kx, ky;
+        item_of(item, A.nxs, A.nfull, kx, ky);
+        const int fi = ky * A.nxs + kx;
+        bool dry = false;
+        if (A.fl_in) {
+            // an item whose 3x3 neighbourhood of items held no wet cell (a radius
+            // of at least 2 cells) keeps its values; if its other copy already
+            // holds them too, the item is skipped
+            dry = !(((A.inflow_mask >> SIDE_W) & 1) && kx == 0) && !(((A.inflow_mask >> SIDE_E) & 1) && kx == A.nxs - 1) &&
+                  !(((A.inflow_mask >> SIDE_S) & 1) && ky == 0) && !(((A.inflow_mask >> SIDE_N) & 1) && ky == A.nys - 1);
+            for (int dy = -1; dy <= 1 && dry; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qx = kx + dx, qy = ky + dy;
+                    if (qx >= 0 && qy >= 0 && qx < A.nxs && qy < A.nys) dry = dry && (A.fl_in[qy * A.nxs + qx] & 1u);
+                }
+            if (dry && (A.fl_in[fi] & 2u)) {
+                if (lane == 0) A.fl_out[fi] = 3u;
+                item = __shfl_sync(FULL, nxt, 0);
+                continue;
+            }
+        }
         const int x0 = kx * Geo<T, CPT>::OUT;
         I.xw = SX > 0 ? x0 - CPT : x0;
         I.xb = (I.xw - 2) & ~(Geo<T, CPT>::ALIGN - 1);
@@ -714,7 +781,9 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         I.y1 = min(A.G.ny, I.y0 + A.L);
         I.nr = I.y1 - I.y0 + 4;
         I.edge = (I.xw - 2 < 0) || (I.xw + Geo<T, CPT>::W + 1 > A.G.nx - 1);
-        run_item<T, CPT, SX, SY, KAPPA>(A, S, acc, I, Cy, &tme, &tmu, &tmv, &tmz, timed_out);
+        const bool wet = run_item<T, CPT, SX, SY, KAPPA>(A, S, acc, I, Cy, &tme, &tmu, &tmv, &tmz, timed_out);
+        if (A.fl_in && lane == 0) A.fl_out[fi] = (wet ? 0u : 1u) | (dry ? 2u : 0u);
+        item = __shfl_sync(FULL, nxt, 0);
     }
 
     // ---- reductions: warp, CTA, then one atomic per CTA
@@ -762,6 +831,7 @@ namespace fz {
 struct Plan {
     CUtensorMap e[2], u[2], v[2], z;
     int nxs, nys, L, nitems, grid;
+    unsigned* flags;  // [2][nitems] dry-skip flags by step parity (device)
     bool ready;
 };
 
@@ -786,7 +856,14 @@ cudaError_t launch_t(swe_ctx* c, const Plan& pl, int s, long long k) {
     A.dx = p.dx; A.dy = p.dy; A.g = p.g; A.cfl = p.cfl; A.dt_max = p.dt_max; A.area = p.dx * p.dy;
     A.s = s;
     A.slot_cur = (int)(k % 3); A.slot_next = (int)((k + 1) % 3); A.slot_zero = (int)((k + 2) % 3);
-    A.nxs = pl.nxs; A.nys = pl.nys; A.L = pl.L; A.nitems = pl.nitems;
+    A.nxs = pl.nxs; A.nys = pl.nys; A.L = pl.L; A.nitems = pl.nitems; A.nfull = p.ny / pl.L;
+    A.fl_in = nullptr; A.fl_out = nullptr; A.inflow_mask = 0;
+    if (p.dry_skip && pl.flags) {
+        A.fl_in = pl.flags + (size_t)(k & 1) * pl.nitems;
+        A.fl_out = pl.flags + (size_t)((k + 1) & 1) * pl.nitems;
+        for (int q = 0; q < 4; ++q)
+            if (p.bc[q] == SWE_BC_INFLOW) A.inflow_mask |= 1 << q;
+    }
     auto kern = k_fused<T, CPT, SX, SY, KAPPA>;
     constexpr int SM = cpt_smem<T, CPT>();
     static bool attr_done = false;

@@ -18,6 +18,8 @@ struct DevCtl {
     unsigned int flags;
     unsigned int pad;
     double dt_cur;               // plain path: step size of the current step
+    unsigned int qctr[3];        // fused path: work-queue counter, slot k%3 = step k
+    unsigned int pad2;
 };
 
 // Per-call diagnostics reduction result.
@@ -79,6 +81,9 @@ struct swe_ctx {
 cudaError_t swe_launch_plain_step(swe_ctx* c, int s, long long k);
 cudaError_t swe_launch_fused_step(swe_ctx* c, int s, long long k);
 cudaError_t swe_fused_prepare(swe_ctx* c);
+cudaError_t swe_fused_reset_flags(swe_ctx* c);
+void swe_fused_release(swe_ctx* c);  // frees the work plan and its device flags
+int swe_fused_row_candidates(swe_ctx* c, int* out, int cap);
 cudaError_t swe_launch_prologue(swe_ctx* c);
 cudaError_t swe_launch_diag(swe_ctx* c);
 cudaError_t swe_launch_to_real(swe_ctx* c, const double* src, void* dst, int n_planes, bool square_n);

@@ -143,6 +143,7 @@ __global__ void k_call_begin(DevCtl* ctl) {
     ctl->dt_min = 1e300;
     ctl->dt_maxs = 0.0;
     ctl->flags = 0u;
+    ctl->qctr[0] = ctl->qctr[1] = ctl->qctr[2] = 0u;
 }
 
 }  // namespace swe
@@ -243,7 +244,9 @@ cudaError_t swe_launch_diag(swe_ctx* c) {
 
 cudaError_t swe_launch_call_begin(swe_ctx* c) {
     k_call_begin<<<1, 1, 0, c->stream>>>(c->ctl);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = swe_fused_reset_flags(c);
+    return e;
 }
 
 // One plain FP32 step on caller-provided dense buffers (row pitch `pitch`)
@@ -269,10 +272,10 @@ cudaError_t swe_plain_step_f32_raw(const swe_params* p, int pitch, const float* 
     const double area = p->dx * p->dy;
 #define SWE_RAW_STEP(SX_, SY_)                                                                                   \
     do {                                                                                                         \
-        k_plain_pred<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, p->dx, p->dy, p->g, e, u, v, z, nullptr,      \
-                                                           ps_e, ps_u, ps_v, ctl, area);                         \
-        k_plain_corr<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, p->dx, p->dy, p->g, e, u, v, z, nullptr,      \
-                                                           ps_e, ps_u, ps_v, e1, u1, v1, 1, area);               \
+        k_plain_pred<float, SX_, SY_><<<grd, blk, 0, st>>>(G, &ctl->dt_cur, p->dx, p->dy, p->g, e, u, v, z,     \
+                                                           nullptr, ps_e, ps_u, ps_v, ctl, area);                \
+        k_plain_corr<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, &ctl->dt_cur, p->dx, p->dy, p->g, e, u, v, z, \
+                                                           nullptr, ps_e, ps_u, ps_v, e1, u1, v1, 1, area);      \
     } while (0)
     if (sx > 0 && sy > 0) SWE_RAW_STEP(1, 1);
     else if (sx > 0) SWE_RAW_STEP(1, -1);

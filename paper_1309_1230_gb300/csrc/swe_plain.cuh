@@ -44,7 +44,7 @@ static __global__ void k_plain_dt(DevCtl* ctl, int slot, int slot_next, const do
 }
 
 template <class T, int SX, int SY>
-__global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const DevCtl* __restrict__ ctl, double dx,
+__global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __restrict__ dtp, double dx,
                                                     double dy, double g, const T* __restrict__ e,
                                                     const T* __restrict__ u, const T* __restrict__ v,
                                                     const T* __restrict__ z, const T* __restrict__ n2,
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const DevCtl* __
                                                     T* __restrict__ vs, DevCtl* ctl_w, double area) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const StepK<T> S = make_stepk<T>(ctl->dt_cur, dx, dy, g);
+    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
     T added = T(0);
     if (i < G.nx && j < G.ny) {
         const size_t k = (size_t)j * G.pitch + i;
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const DevCtl* __
 }
 
 template <class T, int SX, int SY>
-__global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, double dx, double dy, double g,
+__global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, const double* __restrict__ dtp,
+                                                    double dx, double dy, double g,
                                                     const T* __restrict__ e, const T* __restrict__ u,
                                                     const T* __restrict__ v, const T* __restrict__ z,
                                                     const T* __restrict__ n2, const T* __restrict__ es,
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, dou
     constexpr int CX = -SX, CY = -SY;  // corrector directions
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const double dtd = ctl->dt_cur;
+    const double dtd = *dtp;
     const StepK<T> S = make_stepk<T>(dtd, dx, dy, g);
     T added = T(0), speed = T(0);
     double bw = 0.0, be = 0.0, bs = 0.0, bn = 0.0;
@@ -195,10 +196,10 @@ static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
     const int a = c->cur, b = 1 - c->cur;
     const double area = p.dx * p.dy;
     k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(
-        G, c->ctl, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        G, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (T*)c->ps[0], (T*)c->ps[1], (T*)c->ps[2], c->ctl, area);
     k_plain_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(
-        G, c->ctl, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        G, c->ctl, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (const T*)c->ps[0], (const T*)c->ps[1], (const T*)c->ps[2], (T*)c->eta[b], (T*)c->u[b],
         (T*)c->v[b], slot_next, area);
     return cudaGetLastError();

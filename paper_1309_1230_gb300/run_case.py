@@ -22,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--kernel", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--seg-rows", type=int, default=0, help="rows per work item (0: automatic)")
+    ap.add_argument("--dry-skip", type=int, default=1, choices=[0, 1], help="skip all-dry work items")
     a = ap.parse_args(argv)
 
     import torch
@@ -38,7 +40,7 @@ def main(argv=None):
     prec = swe.SWE_FP32 if a.precision == "fp32" else swe.SWE_FP64
     kern = swe.SWE_KERNEL_FUSED if a.kernel == "fused" else swe.SWE_KERNEL_PLAIN
     s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=case["kappa"], bc=case["bc"],
-                   q_in=case["q_in"], precision=prec, kernel=kern)
+                   q_in=case["q_in"], precision=prec, kernel=kern, seg_rows=a.seg_rows, dry_skip=a.dry_skip)
     s.set_bed(case["z"])
     s.set_state(case["eta"], case["u"], case["v"])
     s.step(a.warmup, want_info=False)
@@ -52,6 +54,7 @@ def main(argv=None):
     ms = e0.elapsed_time(e1) / max(1, a.steps)
     info = s.info()
     print(json.dumps({"case": a.case, "n": a.n, "precision": a.precision, "kernel": a.kernel, "steps": a.steps,
+                      "seg_rows": a.seg_rows, "dry_skip": a.dry_skip,
                       "ms_per_step": ms, "cell_updates_per_s": case["nx"] * case["ny"] / (ms / 1e3),
                       "volume": info.volume, "t": info.t, "time": time.time()}))
     s.close()

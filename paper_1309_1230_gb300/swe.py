@@ -93,6 +93,12 @@ _SIGS = {
     "swe_batch_last_error": (ctypes.c_char_p, [_vp]),
     "swe_adjoint": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _dp,
                                    ctypes.c_int32, _dp, _dp, _dp]),
+    "swe_autotune_candidates": (ctypes.c_int32, [_ctxp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "swe_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _dp,
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "swe_batch_autotune_candidates": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "swe_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _dp,
+                                          ctypes.POINTER(ctypes.c_int32)]),
 }
 
 
@@ -265,6 +271,23 @@ class Solver:
         _check(st, self.ctx)
         return float(loss[0]), gn, ge
 
+    def autotune(self, probe_steps: int = 10, rows=None):
+        """Times each candidate rows-per-item of the fused step on the current
+        state (which is restored) and keeps the fastest; returns (chosen,
+        {rows: ms per step})."""
+        if rows is None:
+            buf = (ctypes.c_int32 * 16)()
+            n = self.lib.swe_autotune_candidates(self.ctx, buf, 16)
+            if n < 0:
+                _check(-n, self.ctx)
+            rows = list(buf[:n])
+        cand = (ctypes.c_int32 * len(rows))(*[int(r) for r in rows])
+        ms = np.zeros(len(rows))
+        chosen = ctypes.c_int32(0)
+        _check(self.lib.swe_autotune(self.ctx, int(probe_steps), cand, len(rows), _p(ms), ctypes.byref(chosen)),
+               self.ctx)
+        return int(chosen.value), dict(zip([int(r) for r in rows], ms.tolist()))
+
     # torch tensors on the context's device, of the context's real type
     def set_state_device(self, eta, u, v):
         for a in (eta, u, v):
@@ -336,6 +359,21 @@ class Batch:
         infos = (swe_step_info * self.count)() if want_info else None
         self._chk(self.lib.swe_batch_step(self.b, int(nsteps), infos))
         return [_info(x) for x in infos] if want_info else None
+
+    def autotune(self, probe_steps: int = 10, rows=None):
+        """Times each candidate rows-per-item on the current states (which are
+        restored) and keeps the fastest; returns (chosen, {rows: ms per step})."""
+        if rows is None:
+            buf = (ctypes.c_int32 * 16)()
+            n = self.lib.swe_batch_autotune_candidates(self.b, buf, 16)
+            if n < 0:
+                self._chk(-n)
+            rows = list(buf[:n])
+        cand = (ctypes.c_int32 * len(rows))(*[int(r) for r in rows])
+        ms = np.zeros(len(rows))
+        chosen = ctypes.c_int32(0)
+        self._chk(self.lib.swe_batch_autotune(self.b, int(probe_steps), cand, len(rows), _p(ms), ctypes.byref(chosen)))
+        return int(chosen.value), dict(zip([int(r) for r in rows], ms.tolist()))
 
     def get_state(self, i):
         sh = self._shape(i)

@@ -129,3 +129,28 @@ def test_autograd_function():
     s.close()
     assert float(loss.detach()) == l2
     assert np.array_equal(n_t.grad.numpy(), gn) and np.array_equal(e_t.grad.numpy(), ge)
+
+
+def test_gpu_adjoint_rejects_runs_outside_its_regime():
+    """The adjoint differentiates the fully wet, kappa = 0 step: a dry cell
+    anywhere in the run, or dissipation, is refused (SWE_ERR_UNSUPPORTED)."""
+    from paper_1309_1230_gb300 import swe
+    c, nfield = _case()
+    T = 10
+    obs = _obs(c, T)
+    c_dry = dict(c)
+    c_dry["eta"] = c["eta"].copy()
+    c_dry["eta"][5, 7] = c["z"][5, 7]
+    for prec in (swe.SWE_FP64, swe.SWE_FP32):
+        s = _solver(c_dry, nfield, prec)
+        with pytest.raises(swe.SweError) as ei:
+            s.adjoint(T, c["gauges"], obs)
+        assert ei.value.status == swe.SWE_ERR_UNSUPPORTED
+        s.close()
+    s = swe.Solver(c["nx"], c["ny"], manning_n=0.03, kappa=0.25, precision=swe.SWE_FP64)
+    s.set_bed(c["z"], nfield)
+    s.set_state(c["eta"], c["u"], c["v"])
+    with pytest.raises(swe.SweError) as ei:
+        s.adjoint(T, c["gauges"], obs)
+    assert ei.value.status == swe.SWE_ERR_UNSUPPORTED
+    s.close()

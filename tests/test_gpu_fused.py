@@ -86,6 +86,27 @@ def test_fused_independent_of_decomposition(name, precision):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_dry_skip_bitwise(precision):
+    """Skipping all-dry work items (their 3x3 item neighbourhood held no wet
+    cell and their other copy already agrees) leaves the state bitwise equal
+    to computing every item, in one call or several, with short items so that
+    most of the dry half is skipped until the front arrives."""
+    from paper_1309_1230_gb300 import swe
+    case = I.dam_break(400, 120, seed=21)
+    steps = 160
+    ref = _run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=16, dry_skip=0)
+    one = _run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=16, dry_skip=1)
+    s = gpu_solver(case, precision, swe.SWE_KERNEL_FUSED, seg_rows=16, dry_skip=1)
+    d1 = s.step(40, want_dt=True)[1]
+    d2 = s.step(steps - 40, want_dt=True)[1]
+    split = s.get_state()
+    s.close()
+    assert np.array_equal(one[1], ref[1]) and np.array_equal(np.concatenate([d1, d2]), ref[1])
+    for a, b, c in zip(one[2:], ref[2:], split):
+        assert np.array_equal(a, b) and np.array_equal(c, b)
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 7), (9, 1), (3, 3), (130, 5), (5, 130), (125, 4), (124, 3)])
 def test_fused_small_and_degenerate_grids(oracle, shape):
     from paper_1309_1230_gb300 import swe
@@ -170,3 +191,33 @@ def test_fused_dt_replay(oracle):
     assert np.array_equal(dts, ref.dt)
     emax, _ = rel_depth_err(e - case["z"], ref.eta - case["z"])
     assert emax <= 1e-4
+
+
+def test_autotune_keeps_the_state_and_the_results():
+    """The work-item autotuner times candidate heights on the live state and
+    restores it: the clock does not move and later steps are bitwise those
+    of a context that was never tuned."""
+    from paper_1309_1230_gb300 import swe
+    case = CASES["dambreak"][0]()
+    tuned = gpu_solver(case, swe.SWE_FP32, swe.SWE_KERNEL_FUSED)
+    tuned.step(5)
+    before = tuned.info()
+    chosen, table = tuned.autotune(probe_steps=3)
+    after = tuned.info()
+    assert chosen in table and all(ms > 0 for ms in table.values()), table
+    assert (after.t, after.step, after.clamp_volume) == (before.t, before.step, before.clamp_volume)
+    chosen2, table2 = tuned.autotune(probe_steps=2, rows=[16, 40])
+    assert chosen2 in (16, 40) and set(table2) == {16, 40}
+    tuned.step(60)
+    plain = gpu_solver(case, swe.SWE_FP32, swe.SWE_KERNEL_FUSED)
+    plain.step(65)
+    for a, b in zip(tuned.get_state(), plain.get_state()):
+        assert np.array_equal(a, b)
+    assert tuned.info().t == plain.info().t
+    tuned.close()
+    plain.close()
+    p = gpu_solver(case, swe.SWE_FP32, swe.SWE_KERNEL_PLAIN)
+    with pytest.raises(swe.SweError) as ei:
+        p.autotune()
+    assert ei.value.status == swe.SWE_ERR_UNSUPPORTED
+    p.close()
