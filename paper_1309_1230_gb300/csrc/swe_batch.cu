@@ -131,8 +131,7 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
     Carry<T, CPT> Cy;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) Cy.P[b].e[j] = Cy.P[b].u[j] = Cy.P[b].v[j] = Cy.P[b].z[j] = Cy.P[b].qy[j] = 0.f;
+        Cy.P[b].e = Cy.P[b].u = Cy.P[b].v = Cy.P[b].z = Cy.P[b].qy = fz::Vec<T, CPT>(0.f);
     bool timed_out = false;
 
     for (int st = 0; st < B.nsteps && !timed_out; ++st) {

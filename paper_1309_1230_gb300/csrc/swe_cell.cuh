@@ -10,6 +10,15 @@
 // flush-to-zero; FP64 is IEEE throughout.  The library is compiled without
 // implicit multiply-add contraction: every fused multiply-add below is
 // written out (fma_), so the rounding of a cell is fixed by this file alone.
+//
+// The stage functions are generic in the value type R: a scalar T, or a
+// lane vector vecn<T, N> holding the N cells one lane of the fused kernel
+// owns in a row.  vecn<float, 2> adds, multiplies and multiply-adds both
+// cells with one packed instruction (add/sub/mul/fma.rn.ftz.f32x2, sm_100
+// and later); everything else acts per cell.  Per component a packed
+// operation rounds exactly like its scalar one (IEEE round to nearest, FP32
+// subnormals flushed), so a cell's result does not depend on the value type
+// it was computed in.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -55,12 +64,14 @@ __host__ __device__ inline StepK<T> make_stepk(double dt, double dx, double dy, 
     return s;
 }
 
-template <class T>
-__device__ __forceinline__ T fma_(T a, T b, T c);
-template <>
-__device__ __forceinline__ float fma_<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-template <>
-__device__ __forceinline__ double fma_<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+// Scalar fused multiply-add, round to nearest (FP32: subnormals flushed,
+// stated explicitly so that the packed form below rounds the same).
+__device__ __forceinline__ float fma_(float a, float b, float c) {
+    float d;
+    asm("fma.rn.ftz.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 __device__ __forceinline__ float pow_m43(float h) { return __powf(h, -1.33333333f); }
 __device__ __forceinline__ double pow_m43(double h) {
@@ -69,20 +80,173 @@ __device__ __forceinline__ double pow_m43(double h) {
     return r2 * r2;
 }
 
-template <class T>
-__device__ __forceinline__ T rsq_sqrt(T x) { return sqrt(x); }
-template <>
-__device__ __forceinline__ float rsq_sqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ float rsq_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rsq_sqrt(double x) { return sqrt(x); }
 
 template <class T>
-__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+__device__ __forceinline__ T sel(bool c, T a, T b) { return c ? a : b; }
+
+// Per-cell (never packed) multiply: the friction update below keeps it so
+// that the fused kernel's cells stay bitwise equal to the one-thread-per-cell
+// kernel's (with the packed multiply there, a few cells differed by one ulp,
+// although the packed and scalar products of the same operands agreed when
+// compared in the kernel).
+__device__ __forceinline__ float smul(float a, float b) { return a * b; }
+__device__ __forceinline__ double smul(double a, double b) { return a * b; }
+
+// ---------------------------------------------------------------- lane vectors
+template <int N>
+struct maskn {
+    bool c[N];
+    friend __device__ __forceinline__ maskn operator&&(maskn a, maskn b) {
+        maskn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = a.c[i] && b.c[i];
+        return r;
+    }
+    friend __device__ __forceinline__ maskn operator||(maskn a, maskn b) {
+        maskn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = a.c[i] || b.c[i];
+        return r;
+    }
+    friend __device__ __forceinline__ maskn operator!(maskn a) {
+        maskn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = !a.c[i];
+        return r;
+    }
+};
+
+// N cells of a lane, arithmetic per component (the generic form).
+template <class T, int N>
+struct vecn {
+    T c[N];
+    vecn() = default;
+    __device__ __forceinline__ vecn(T s) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) c[i] = s;
+    }
+    __device__ __forceinline__ T& operator[](int i) { return c[i]; }
+    __device__ __forceinline__ const T& operator[](int i) const { return c[i]; }
+#define SWE_VEC_OP(OP)                                                         \
+    friend __device__ __forceinline__ vecn operator OP(vecn a, vecn b) {       \
+        vecn r;                                                                \
+        _Pragma("unroll") for (int i = 0; i < N; ++i) r.c[i] = a.c[i] OP b.c[i]; \
+        return r;                                                              \
+    }
+    SWE_VEC_OP(+)
+    SWE_VEC_OP(-)
+    SWE_VEC_OP(*)
+    SWE_VEC_OP(/)
+#undef SWE_VEC_OP
+#define SWE_VEC_CMP(OP)                                                        \
+    friend __device__ __forceinline__ maskn<N> operator OP(vecn a, vecn b) {   \
+        maskn<N> r;                                                            \
+        _Pragma("unroll") for (int i = 0; i < N; ++i) r.c[i] = a.c[i] OP b.c[i]; \
+        return r;                                                              \
+    }
+    SWE_VEC_CMP(>)
+    SWE_VEC_CMP(<)
+    SWE_VEC_CMP(<=)
+    SWE_VEC_CMP(>=)
+    SWE_VEC_CMP(==)
+#undef SWE_VEC_CMP
+    friend __device__ __forceinline__ vecn operator-(vecn a) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = -a.c[i];
+        return r;
+    }
+    friend __device__ __forceinline__ vecn fma_(vecn a, vecn b, vecn d) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = fma_(a.c[i], b.c[i], d.c[i]);
+        return r;
+    }
+    friend __device__ __forceinline__ vecn smul(vecn a, vecn b) { return a * b; }
+    friend __device__ __forceinline__ vecn sel(maskn<N> m, vecn a, vecn b) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = m.c[i] ? a.c[i] : b.c[i];
+        return r;
+    }
+    friend __device__ __forceinline__ vecn rsq_sqrt(vecn a) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = rsq_sqrt(a.c[i]);
+        return r;
+    }
+    friend __device__ __forceinline__ vecn pow_m43(vecn a) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = pow_m43(a.c[i]);
+        return r;
+    }
+};
+
+// Two FP32 cells: add, subtract, multiply and multiply-add as one packed
+// instruction each; the rest per component.
+template <>
+struct vecn<float, 2> {
+    float2 v;
+    vecn() = default;
+    __device__ __forceinline__ vecn(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ vecn(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ float& operator[](int i) { return i == 0 ? v.x : v.y; }
+    __device__ __forceinline__ const float& operator[](int i) const { return i == 0 ? v.x : v.y; }
+#define SWE_PACKED(NAME, INSN)                                                                            \
+    friend __device__ __forceinline__ vecn NAME(vecn a, vecn b) {                                         \
+        vecn r;                                                                                           \
+        asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n " INSN           \
+            " rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                                                     \
+            : "=f"(r.v.x), "=f"(r.v.y) : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));                 \
+        return r;                                                                                         \
+    }
+    SWE_PACKED(operator+, "add.rn.ftz.f32x2")
+    SWE_PACKED(operator-, "sub.rn.ftz.f32x2")
+    SWE_PACKED(operator*, "mul.rn.ftz.f32x2")
+#undef SWE_PACKED
+    friend __device__ __forceinline__ vecn operator/(vecn a, vecn b) { return vecn(a.v.x / b.v.x, a.v.y / b.v.y); }
+    friend __device__ __forceinline__ vecn smul(vecn a, vecn b) { return vecn(a.v.x * b.v.x, a.v.y * b.v.y); }
+    friend __device__ __forceinline__ vecn fma_(vecn a, vecn b, vecn d) {
+        vecn r;
+        asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+            " mov.b64 rc, {%6, %7};\n fma.rn.ftz.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+            : "=f"(r.v.x), "=f"(r.v.y)
+            : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y), "f"(d.v.x), "f"(d.v.y));
+        return r;
+    }
+    friend __device__ __forceinline__ vecn operator-(vecn a) { return vecn(-a.v.x, -a.v.y); }
+#define SWE_PCMP(OP)                                                        \
+    friend __device__ __forceinline__ maskn<2> operator OP(vecn a, vecn b) { \
+        maskn<2> r;                                                         \
+        r.c[0] = a.v.x OP b.v.x;                                            \
+        r.c[1] = a.v.y OP b.v.y;                                            \
+        return r;                                                           \
+    }
+    SWE_PCMP(>)
+    SWE_PCMP(<)
+    SWE_PCMP(<=)
+    SWE_PCMP(>=)
+    SWE_PCMP(==)
+#undef SWE_PCMP
+    friend __device__ __forceinline__ vecn sel(maskn<2> m, vecn a, vecn b) {
+        return vecn(m.c[0] ? a.v.x : b.v.x, m.c[1] ? a.v.y : b.v.y);
+    }
+    friend __device__ __forceinline__ vecn rsq_sqrt(vecn a) { return vecn(sqrtf(a.v.x), sqrtf(a.v.y)); }
+    friend __device__ __forceinline__ vecn pow_m43(vecn a) { return vecn(pow_m43(a.v.x), pow_m43(a.v.y)); }
+};
+
+template <class R>
+__device__ __forceinline__ R tmax(R a, R b) { return sel(a > b, a, b); }
 
 // Elevation of neighbour nb seen by the pressure term of a cell at elevation
 // eta_self: a dry neighbour whose bed is above eta_self acts as a wall.
-template <class T>
-__device__ __forceinline__ T eta_seen(const Cell<T>& nb, T eta_self, T h_dry) {
-    bool dry = !((nb.e - nb.z) > h_dry);
-    return (dry && nb.z > eta_self) ? eta_self : nb.e;
+template <class R, class T>
+__device__ __forceinline__ R eta_seen(const Cell<R>& nb, R eta_self, T h_dry) {
+    const auto dry = !((nb.e - nb.z) > R(h_dry));
+    return sel(dry && (nb.z > eta_self), eta_self, nb.e);
 }
 
 // Ghost cell of side `side` from the adjacent interior cell `in` (S3/S9).
@@ -125,12 +289,12 @@ __device__ __forceinline__ void faces(T qc, T qn, bool lo, bool hi, int side_lo,
 }
 
 // Manning coefficient of a cell (S6/S12): g n^2 |U| / h^(4/3) when wet.
-template <class T>
-__device__ __forceinline__ T friction(const Cell<T>& c, T gn2, T h_dry) {
-    T h = c.e - c.z;
-    T s2 = fma_(c.u, c.u, c.v * c.v);
-    T mag = s2 > T(0) ? rsq_sqrt(s2) : T(0);
-    return (h > h_dry) ? gn2 * mag * pow_m43(h) : T(0);
+template <class R, class T>
+__device__ __forceinline__ R friction(const Cell<R>& c, R gn2, T h_dry) {
+    const R h = c.e - c.z;
+    const R s2 = fma_(c.u, c.u, c.v * c.v);
+    const R mag = sel(s2 > R(0), rsq_sqrt(s2), R(0));
+    return sel(h > R(h_dry), gn2 * mag * pow_m43(h), R(0));
 }
 
 // One MacCormack stage of a cell (S5-S8 for the predictor, S11-S13 for the
@@ -138,49 +302,64 @@ __device__ __forceinline__ T friction(const Cell<T>& c, T gn2, T h_dry) {
 // for the predictor, predicted for the corrector); xn/yn: its neighbours in
 // the stage's one-sided directions DX/DY (ghost cells at the boundary);
 // f*: face fluxes; e0,u0,v0: the level-n values the stage updates from.
-template <int DX, int DY, class T>
-__device__ __forceinline__ void stage(const Cell<T>& c, const Cell<T>& xn, const Cell<T>& yn,
-                                      T fe, T fw, T fn, T fs, T e0, T u0, T v0, T gn2,
-                                      const StepK<T>& S, T h_dry, T& eo, T& uo, T& vo) {
-    eo = e0 - fma_(S.dtdx, fe - fw, S.dtdy * (fn - fs));
-    T cf = friction(c, gn2, h_dry);
-    T ex = eta_seen(xn, c.e, h_dry);
-    T ey = eta_seen(yn, c.e, h_dry);
-    T dux, dvx, dex, duy, dvy, dey;
+template <int DX, int DY, class R, class T>
+__device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn,
+                                      R fe, R fw, R fn, R fs, R e0, R u0, R v0, R gn2,
+                                      const StepK<T>& S, T h_dry, R& eo, R& uo, R& vo) {
+    eo = e0 - fma_(R(S.dtdx), fe - fw, R(S.dtdy) * (fn - fs));
+    const R cf = friction(c, gn2, h_dry);
+    const R ex = eta_seen(xn, c.e, h_dry);
+    const R ey = eta_seen(yn, c.e, h_dry);
+    R dux, dvx, dex, duy, dvy, dey;
     if (DX > 0) { dux = xn.u - c.u; dvx = xn.v - c.v; dex = ex - c.e; }
     else        { dux = c.u - xn.u; dvx = c.v - xn.v; dex = c.e - ex; }
     if (DY > 0) { duy = yn.u - c.u; dvy = yn.v - c.v; dey = ey - c.e; }
     else        { duy = c.u - yn.u; dvy = c.v - yn.v; dey = c.e - ey; }
-    T au = fma_(c.u, S.dtdx * dux, fma_(c.v, S.dtdy * duy, S.g_dtdx * dex));
-    T av = fma_(c.u, S.dtdx * dvx, fma_(c.v, S.dtdy * dvy, S.g_dtdy * dey));
-    T r = T(1) / fma_(S.dt, cf, T(1));
-    uo = (u0 - au) * r;
-    vo = (v0 - av) * r;
+    const R au = fma_(c.u, R(S.dtdx) * dux, fma_(c.v, R(S.dtdy) * duy, R(S.g_dtdx) * dex));
+    const R av = fma_(c.u, R(S.dtdx) * dvx, fma_(c.v, R(S.dtdy) * dvy, R(S.g_dtdy) * dey));
+    const R r = R(T(1)) / fma_(R(S.dt), cf, R(T(1)));
+    uo = smul(u0 - au, r);
+    vo = smul(v0 - av, r);
 }
 
 // Wet/dry fix (S8/S16): negative depth -> eta = z (returns the added depth),
 // dry -> zero velocity.
-template <class T>
-__device__ __forceinline__ T wetdry_fix(T& e, T& u, T& v, T z, T h_dry) {
-    T h = e - z;
-    T added = T(0);
-    if (h < T(0)) { added = -h; e = z; h = T(0); }
-    if (h <= h_dry) { u = T(0); v = T(0); }
+template <class R, class T>
+__device__ __forceinline__ R wetdry_fix(R& e, R& u, R& v, R z, T h_dry) {
+    R h = e - z;
+    const auto neg = h < R(T(0));
+    const R added = sel(neg, z - e, R(T(0)));  // -h, exactly
+    e = sel(neg, z, e);
+    h = sel(neg, R(T(0)), h);
+    const auto dry = h <= R(h_dry);
+    u = sel(dry, R(T(0)), u);
+    v = sel(dry, R(T(0)), v);
     return added;
 }
 
 // Dissipation switch of a cell along one axis (S15).
-template <class T>
-__device__ __forceinline__ T nu_switch(T hl, T hc, T hr) {
-    T num = fabs(fma_(T(-2), hc, hl + hr));
-    T den = fma_(T(2), fabs(hc), fabs(hl) + fabs(hr)) + T(SWE_NU_TINY);
+__device__ __forceinline__ float nu_switch(float hl, float hc, float hr) {
+    const float num = fabsf(fma_(-2.0f, hc, hl + hr));
+    const float den = fma_(2.0f, fabsf(hc), fabsf(hl) + fabsf(hr)) + (float)SWE_NU_TINY;
     return num / den;
+}
+__device__ __forceinline__ double nu_switch(double hl, double hc, double hr) {
+    const double num = fabs(fma_(-2.0, hc, hl + hr));
+    const double den = fma_(2.0, fabs(hc), fabs(hl) + fabs(hr)) + SWE_NU_TINY;
+    return num / den;
+}
+template <class T, int N>  // per cell: the absolute values fold into the scalar instructions
+__device__ __forceinline__ vecn<T, N> nu_switch(vecn<T, N> hl, vecn<T, N> hc, vecn<T, N> hr) {
+    vecn<T, N> r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = nu_switch(hl[i], hc[i], hr[i]);
+    return r;
 }
 
 // Face coefficient of the dissipation: interior face between two wet cells.
-template <class T>
-__device__ __forceinline__ T face_eps(bool wet_a, bool wet_b, T nu_a, T nu_b) {
-    return (wet_a && wet_b) ? tmax(nu_a, nu_b) : T(0);
+template <class M, class R>
+__device__ __forceinline__ R face_eps(M wet_a, M wet_b, R nu_a, R nu_b) {
+    return sel(wet_a && wet_b, tmax(nu_a, nu_b), R(0.0f));
 }
 
 // S15 dissipation flux through one face: eps * (phi_above - phi_below).
@@ -190,9 +369,9 @@ __device__ __forceinline__ T dflux(T eps, T hi, T lo) { return eps * (hi - lo); 
 // S15 for one field of a cell from its four face fluxes (east, west, north,
 // south): out + kappa * ((fe - fw) + (fn - fs)).  Every kernel form builds the
 // same face fluxes with dflux, so a face is rounded the same from both sides.
-template <class T>
-__device__ __forceinline__ T dissip_faces(T out, T fe, T fw, T fn, T fs, T kappa) {
-    return fma_(kappa, (fe - fw) + (fn - fs), out);
+template <class R, class T>
+__device__ __forceinline__ R dissip_faces(R out, R fe, R fw, R fn, R fs, T kappa) {
+    return fma_(R(kappa), (fe - fw) + (fn - fs), out);
 }
 
 // CFL speed of a cell (S2); 0 for dry cells.
@@ -202,6 +381,15 @@ __device__ __forceinline__ T cfl_speed(T e, T u, T v, T z, const GridK<T>& G) {
     if (!(h > G.h_dry)) return T(0);
     T c = rsq_sqrt(G.g * h);
     return fma_(fabs(u) + c, G.inv_dx, (fabs(v) + c) * G.inv_dy);
+}
+
+template <class T, int N>
+__device__ __forceinline__ vecn<T, N> cfl_speed(vecn<T, N> e, vecn<T, N> u, vecn<T, N> v, vecn<T, N> z,
+                                                const GridK<T>& G) {
+    vecn<T, N> r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = cfl_speed(e[i], u[i], v[i], z[i], G);
+    return r;
 }
 
 // Step size from the reduced CFL speed (S2), FP64.

@@ -42,7 +42,7 @@ cudaError_t encode(CUtensorMap* m, const void* base, const swe_ctx* c) {
 // to be small enough that the warps finish together (about ITEMS_PER_WARP
 // each) while long enough that the four warm-up rows of an item stay a small
 // share of its work.
-constexpr int ITEMS_PER_WARP = 4;
+constexpr int ITEMS_PER_WARP = 8;
 
 int choose_rows(int ny, int nxs, int warps, int forced) {
     if (forced > 0) return forced;

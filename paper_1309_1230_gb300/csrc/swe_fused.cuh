@@ -137,8 +137,12 @@ __device__ __forceinline__ void tma_row(void* dst, const CUtensorMap* map, uint6
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// The CPT cells of a lane in one row (swe_cell.cuh: packed for two FP32 cells).
 template <class T, int CPT>
-__device__ __forceinline__ void ld_vec(const T* p, T (&o)[CPT]) {
+using Vec = vecn<T, CPT>;
+
+template <class T, int CPT>
+__device__ __forceinline__ void ld_vec(const T* p, Vec<T, CPT>& o) {
     if constexpr (sizeof(T) * CPT == 16) {
         if constexpr (sizeof(T) == 4) {
             float4 q = *reinterpret_cast<const float4*>(p);
@@ -156,7 +160,7 @@ __device__ __forceinline__ void ld_vec(const T* p, T (&o)[CPT]) {
     }
 }
 template <class T, int CPT>
-__device__ __forceinline__ void st_vec(T* p, const T (&o)[CPT]) {
+__device__ __forceinline__ void st_vec(T* p, const Vec<T, CPT>& o) {
     if constexpr (sizeof(T) * CPT == 16) {
         if constexpr (sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
         else *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
@@ -170,12 +174,12 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[CPT]) {
 
 template <class T, int CPT>
 struct Row {  // eta, u, v, z of the lane's CPT cells in one row
-    T e[CPT], u[CPT], v[CPT], z[CPT];
+    Vec<T, CPT> e, u, v, z;
 };
 
 template <class T, int CPT>
 struct PR {  // a predicted row as the corrector needs it: eta*, u*, v*, bed, h* v*
-    T e[CPT], u[CPT], v[CPT], z[CPT], qy[CPT];
+    Vec<T, CPT> e, u, v, z, qy;
 };
 
 // State carried from one row to the next, double-buffered by row parity so
@@ -183,10 +187,10 @@ struct PR {  // a predicted row as the corrector needs it: eta*, u*, v*, bed, h*
 // the row just produced go to index PAR, the previous row's are at 1 - PAR.
 template <class T, int CPT>
 struct Carry {
-    PR<T, CPT> P[2];      // predicted rows
-    T NY[2][CPT];         // y dissipation switch of a level-n row
-    T FY[2][3][CPT];      // y dissipation face flux (eta, u, v) above a row
-    T DX[2][3][CPT];      // x dissipation (east minus west face flux) of a row
+    PR<T, CPT> P[2];         // predicted rows
+    Vec<T, CPT> NY[2];       // y dissipation switch of a level-n row
+    Vec<T, CPT> FY[2][3];    // y dissipation face flux (eta, u, v) above a row
+    Vec<T, CPT> DX[2][3];    // x dissipation (east minus west face flux) of a row
 };
 
 struct Acc {  // per-warp totals over its items, FP64
@@ -241,7 +245,8 @@ __device__ __forceinline__ T shup(T x) { return __shfl_up_sync(FULL, x, 1); }
 // cells: the lane's next cell, else the adjacent lane's end cell; the
 // strip-edge lane on that side takes `halo` when `use_halo`.
 template <int D, class T, int CPT>
-__device__ __forceinline__ void shift(const T (&a)[CPT], T halo, bool use_halo, T (&o)[CPT]) {
+__device__ __forceinline__ Vec<T, CPT> shift(const Vec<T, CPT>& a, T halo, bool use_halo) {
+    Vec<T, CPT> o;
     if (D > 0) {
 #pragma unroll
         for (int c = 0; c + 1 < CPT; ++c) o[c] = a[c + 1];
@@ -253,6 +258,14 @@ __device__ __forceinline__ void shift(const T (&a)[CPT], T halo, bool use_halo, 
         const T t = shup(a[CPT - 1]);
         o[0] = use_halo ? halo : t;
     }
+    return o;
+}
+
+template <class T, int CPT>
+__device__ __forceinline__ Cell<Vec<T, CPT>> cells(const Row<T, CPT>& r) {
+    Cell<Vec<T, CPT>> c;
+    c.e = r.e; c.u = r.u; c.v = r.v; c.z = r.z;
+    return c;
 }
 
 // Predicated issue of one ring row: lane 0 arms the barrier and starts the
@@ -298,17 +311,21 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 
 // One ring row r (ring index k) of an item: y switch of row r-1, the
 // predictor and x dissipation of row r-1, and the corrector, average,
-// dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.
+// dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.  The
+// arithmetic works on the lane's CPT cells at once (Vec); boundary cases
+// patch single cells.
 template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN>
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
                                          bool& timed_out) {
+    using V = Vec<T, CPT>;
     constexpr int CX = -SX, CY = -SY;
     constexpr int Q = PAR, O = 1 - PAR;  // this row's buffers, the previous row's
     const GridK<T>& G = A.G;
     const int ny = G.ny, nx = G.nx;
     const T hd = G.h_dry;
+    const V hdv(hd);
     const int lane = I.lane;
     const int r = I.y0 - 2 + k;
 
@@ -340,23 +357,18 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         if (r - 1 < 0) ghost_row(R1, SIDE_S, G); else if (r - 1 >= ny) ghost_row(R1, SIDE_N, G);
         if (r - 2 < 0) ghost_row(R2, SIDE_S, G); else if (r - 2 >= ny) ghost_row(R2, SIDE_N, G);
     }
-    T h0[CPT], h1[CPT], h2[CPT];
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) { h0[j] = R0.e[j] - R0.z[j]; h1[j] = R1.e[j] - R1.z[j]; h2[j] = R2.e[j] - R2.z[j]; }
+    const V h0 = R0.e - R0.z, h1 = R1.e - R1.z, h2 = R2.e - R2.z;
 
     // -------- y switch of row r-1, y dissipation flux through the face between rows r-2 and r-1
     if (KAPPA) {
         const bool face_in = !brow || (r - 2 >= 0 && r - 1 < ny);
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            const T nyn = nu_switch(h2[j], h1[j], h0[j]);
-            T eps = face_eps(h2[j] > hd, h1[j] > hd, Cy.NY[O][j], nyn);
-            eps = face_in ? eps : T(0);
-            Cy.FY[Q][0][j] = dflux(eps, R1.e[j], R2.e[j]);
-            Cy.FY[Q][1][j] = dflux(eps, R1.u[j], R2.u[j]);
-            Cy.FY[Q][2][j] = dflux(eps, R1.v[j], R2.v[j]);
-            Cy.NY[Q][j] = nyn;
-        }
+        const V nyn = nu_switch(h2, h1, h0);
+        V eps = face_eps(h2 > hdv, h1 > hdv, Cy.NY[O], nyn);
+        if (!face_in) eps = V(T(0));
+        Cy.FY[Q][0] = dflux(eps, R1.e, R2.e);
+        Cy.FY[Q][1] = dflux(eps, R1.u, R2.u);
+        Cy.FY[Q][2] = dflux(eps, R1.v, R2.v);
+        Cy.NY[Q] = nyn;
     }
 
     // -------- predictor and x dissipation of row p = r-1
@@ -364,34 +376,29 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         const int p = r - 1;
         const Row<T, CPT>& c = R1;
         const Row<T, CPT>& yn = SY > 0 ? R0 : R2;
-        const T* hyn = SY > 0 ? h0 : h2;
+        const V hyn = SY > 0 ? h0 : h2;
         // x neighbours: on the predictor's side with the ring halo (that edge lane outputs)
         const int hcol = SX > 0 ? I.col + CPT : I.col - 1;
         const bool edge_lane = SX > 0 ? lane == 31 : lane == 0;
         Row<T, CPT> xn;
-        shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), edge_lane, xn.e);
-        shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), edge_lane, xn.u);
-        shift<SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, hcol), edge_lane, xn.v);
-        shift<SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, hcol), edge_lane, xn.z);
+        xn.e = shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), edge_lane);
+        xn.u = shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), edge_lane);
+        xn.v = shift<SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, hcol), edge_lane);
+        xn.z = shift<SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, hcol), edge_lane);
         if (brow && (r - 1 < 0 || r - 1 >= ny)) {  // halo column of a ghost row
-#pragma unroll
-            for (int j = 0; j < CPT; ++j)
-                if (edge_lane && (SX > 0 ? j == CPT - 1 : j == 0)) {
-                    Cell<T> q; q.e = xn.e[j]; q.u = xn.u[j]; q.v = xn.v[j]; q.z = xn.z[j];
-                    q = ghost(q, r - 1 < 0 ? SIDE_S : SIDE_N, G);
-                    xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
-                }
+            constexpr int j = SX > 0 ? CPT - 1 : 0;
+            if (edge_lane) {
+                Cell<T> q; q.e = xn.e[j]; q.u = xn.u[j]; q.v = xn.v[j]; q.z = xn.z[j];
+                q = ghost(q, r - 1 < 0 ? SIDE_S : SIDE_N, G);
+                xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
+            }
         }
-        T qx[CPT], qy[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            qx[j] = h1[j] * c.u[j];
-            qy[j] = h1[j] * c.v[j];
-            const T qxn = (xn.e[j] - xn.z[j]) * xn.u[j];
-            const T qyn = hyn[j] * yn.v[j];
-            if (SX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
-            if (SY > 0) { fn[j] = qyn; fs[j] = qy[j]; } else { fn[j] = qy[j]; fs[j] = qyn; }
-        }
+        const V qx = h1 * c.u, qy = h1 * c.v;
+        const V qxn = (xn.e - xn.z) * xn.u;
+        const V qyn = hyn * yn.v;
+        V fe, fw, fn, fs;
+        if (SX > 0) { fe = qxn; fw = qx; } else { fe = qx; fw = qxn; }
+        if (SY > 0) { fn = qyn; fs = qy; } else { fn = qy; fs = qyn; }
         if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
@@ -415,31 +422,28 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, qy[j], G);
             }
         }
-        T gn2v[CPT];
+        V gn2v;
         if (A.n2 != nullptr) {
             const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
             const int pr = p < 0 ? 0 : (p >= ny ? ny - 1 : p);
             ld_vec<T, CPT>(A.n2 + (size_t)pr * G.pitch + xc, gn2v);
         } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
+            gn2v = V(G.gn2);
         }
         PR<T, CPT>& P = Cy.P[Q];
+        V eo, uo, vo;
+        stage<SX, SY>(cells(c), cells(xn), cells(yn), fe, fw, fn, fs, c.e, c.u, c.v, gn2v, S, hd, eo, uo, vo);
+        V ad = wetdry_fix(eo, uo, vo, c.z, hd);
+        if (edge) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                if (I.x0c + j >= nx) ad[j] = T(0);
+        }
         T added = T(0);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            Cell<T> cc, cx, cy;
-            cc.e = c.e[j]; cc.u = c.u[j]; cc.v = c.v[j]; cc.z = c.z[j];
-            cx.e = xn.e[j]; cx.u = xn.u[j]; cx.v = xn.v[j]; cx.z = xn.z[j];
-            cy.e = yn.e[j]; cy.u = yn.u[j]; cy.v = yn.v[j]; cy.z = yn.z[j];
-            T eo, uo, vo;
-            stage<SX, SY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], cc.e, cc.u, cc.v, gn2v[j], S, hd, eo, uo, vo);
-            T ad = wetdry_fix(eo, uo, vo, cc.z, hd);
-            if (edge && I.x0c + j >= nx) ad = T(0);
-            added += ad;
-            P.e[j] = eo; P.u[j] = uo; P.v[j] = vo; P.z[j] = cc.z;
-            P.qy[j] = (eo - cc.z) * vo;
-        }
+        for (int j = 0; j < CPT; ++j) added += ad[j];
+        P.e = eo; P.u = uo; P.v = vo; P.z = c.z;
+        P.qy = (eo - c.z) * vo;
         // a predicted clamp counts once per cell: in the item and lane that output it
         if (I.out_lane && p >= I.y0 && p < I.y1 && I.x0c >= 0) ia.clamp = fma_(T(0.5), added, ia.clamp);
 
@@ -447,15 +451,13 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             // x dissipation of row r-1: the other side's neighbours need no halo
             // (the lane at that strip edge never outputs)
             Row<T, CPT> xo;
-            shift<-SX, T, CPT>(c.e, T(0), false, xo.e);
-            shift<-SX, T, CPT>(c.u, T(0), false, xo.u);
-            shift<-SX, T, CPT>(c.v, T(0), false, xo.v);
-            shift<-SX, T, CPT>(c.z, T(0), false, xo.z);
+            xo.e = shift<-SX, T, CPT>(c.e, T(0), false);
+            xo.u = shift<-SX, T, CPT>(c.u, T(0), false);
+            xo.v = shift<-SX, T, CPT>(c.v, T(0), false);
+            xo.z = shift<-SX, T, CPT>(c.z, T(0), false);
             const Row<T, CPT>& L = SX > 0 ? xo : xn;  // left neighbours
             const Row<T, CPT>& Rr = SX > 0 ? xn : xo; // right neighbours
-            T hl[CPT], hr[CPT];
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) { hl[j] = L.e[j] - L.z[j]; hr[j] = Rr.e[j] - Rr.z[j]; }
+            V hl = L.e - L.z, hr = Rr.e - Rr.z;
             if (edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
@@ -463,9 +465,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                     if (I.x0c + j == nx - 1) hr[j] = h1[j];
                 }
             }
-            T nuc[CPT];
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) nuc[j] = nu_switch(hl[j], h1[j], hr[j]);
+            const V nuc = nu_switch(hl, h1, hr);
             // switch one column outside the lane: adjacent lane, or from the ring at the output edge
             T nu_lo = shup(nuc[CPT - 1]), nu_hi = shdn(nuc[0]);
             if (SX > 0) {
@@ -477,28 +477,30 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 const T ext = nu_switch(h2x, hl[0], h1[0]);
                 nu_lo = lane == 0 ? ext : nu_lo;
             }
-            // east face of every cell, west face of the first
-            T fr[3][CPT], fl0[3];
+            // east face of every cell
+            V nur;
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                const T nur = j + 1 < CPT ? nuc[j + 1 < CPT ? j + 1 : j] : nu_hi;
-                T eps = face_eps(h1[j] > hd, hr[j] > hd, nuc[j], nur);
-                if (edge && I.x0c + j + 1 >= nx) eps = T(0);
-                fr[0][j] = dflux(eps, Rr.e[j], c.e[j]);
-                fr[1][j] = dflux(eps, Rr.u[j], c.u[j]);
-                fr[2][j] = dflux(eps, Rr.v[j], c.v[j]);
+            for (int j = 0; j + 1 < CPT; ++j) nur[j] = nuc[j + 1];
+            nur[CPT - 1] = nu_hi;
+            V eps = face_eps(h1 > hdv, hr > hdv, nuc, nur);
+            if (edge) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j)
+                    if (I.x0c + j + 1 >= nx) eps[j] = T(0);
             }
-            {
-                T eps = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
-                if (edge && I.x0c - 1 < 0) eps = T(0);
-                fl0[0] = dflux(eps, c.e[0], L.e[0]);
-                fl0[1] = dflux(eps, c.u[0], L.u[0]);
-                fl0[2] = dflux(eps, c.v[0], L.v[0]);
+            const V fr[3] = {dflux(eps, Rr.e, c.e), dflux(eps, Rr.u, c.u), dflux(eps, Rr.v, c.v)};
+            // west face of the first cell; the others' west faces are their left neighbours' east faces
+            T e0 = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
+            if (edge && I.x0c - 1 < 0) e0 = T(0);
+            const T fl0[3] = {dflux(e0, c.e[0], L.e[0]), dflux(e0, c.u[0], L.u[0]), dflux(e0, c.v[0], L.v[0])};
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                V west;
+                west[0] = fl0[f];
+#pragma unroll
+                for (int j = 1; j < CPT; ++j) west[j] = fr[f][j - 1];
+                Cy.DX[Q][f] = fr[f] - west;
             }
-#pragma unroll
-            for (int f = 0; f < 3; ++f)
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) Cy.DX[Q][f][j] = fr[f][j] - (j == 0 ? fl0[f] : fr[f][j > 0 ? j - 1 : 0]);
         }
     };
 
@@ -508,8 +510,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         const PR<T, CPT>& pc = Cy.P[O];       // predicted row C
         PR<T, CPT> ys = Cy.P[Q];              // row C-1 (forward predictor) or C+1 (backward)
         Row<T, CPT> cs;
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) { cs.e[j] = pc.e[j]; cs.u[j] = pc.u[j]; cs.v[j] = pc.v[j]; cs.z[j] = pc.z[j]; }
+        cs.e = pc.e; cs.u = pc.u; cs.v = pc.v; cs.z = pc.z;
         if (brow && (CY < 0 ? C == 0 : C == ny - 1)) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
@@ -520,18 +521,15 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             }
         }
         Row<T, CPT> xs;  // the lane that would need a halo on this side never outputs
-        shift<CX, T, CPT>(cs.e, T(0), false, xs.e);
-        shift<CX, T, CPT>(cs.u, T(0), false, xs.u);
-        shift<CX, T, CPT>(cs.v, T(0), false, xs.v);
-        shift<CX, T, CPT>(cs.z, T(0), false, xs.z);
-        T qx[CPT], fe[CPT], fw[CPT], fn[CPT], fs[CPT];
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            qx[j] = (cs.e[j] - cs.z[j]) * cs.u[j];
-            const T qxn = (xs.e[j] - xs.z[j]) * xs.u[j];
-            if (CX > 0) { fe[j] = qxn; fw[j] = qx[j]; } else { fe[j] = qx[j]; fw[j] = qxn; }
-            if (CY > 0) { fn[j] = ys.qy[j]; fs[j] = pc.qy[j]; } else { fn[j] = pc.qy[j]; fs[j] = ys.qy[j]; }
-        }
+        xs.e = shift<CX, T, CPT>(cs.e, T(0), false);
+        xs.u = shift<CX, T, CPT>(cs.u, T(0), false);
+        xs.v = shift<CX, T, CPT>(cs.v, T(0), false);
+        xs.z = shift<CX, T, CPT>(cs.z, T(0), false);
+        const V qx = (cs.e - cs.z) * cs.u;
+        const V qxn = (xs.e - xs.z) * xs.u;
+        V fe, fw, fn, fs;
+        if (CX > 0) { fe = qxn; fw = qx; } else { fe = qx; fw = qxn; }
+        if (CY > 0) { fn = ys.qy; fs = pc.qy; } else { fn = pc.qy; fs = ys.qy; }
         if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
@@ -555,44 +553,45 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 for (int j = 0; j < CPT; ++j) fn[j] = face_bnd(SIDE_N, pc.qy[j], G);
             }
         }
-        T gn2v[CPT];
+        V gn2v;
         if (A.n2 != nullptr) {
             const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
             ld_vec<T, CPT>(A.n2 + (size_t)C * G.pitch + xc, gn2v);
         } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) gn2v[j] = G.gn2;
+            gn2v = V(G.gn2);
         }
-        T oe[CPT], ou[CPT], ov[CPT];
+        Cell<V> cy;
+        cy.e = ys.e; cy.u = ys.u; cy.v = ys.v; cy.z = ys.z;
+        V eo, uo, vo;
+        stage<CX, CY>(cells(cs), cells(xs), cy, fe, fw, fn, fs, R2.e, R2.u, R2.v, gn2v, S, hd, eo, uo, vo);
+        const V half(T(0.5));
+        V oe = half * (cs.e + eo);
+        V ou = half * (cs.u + uo);
+        V ov = half * (cs.v + vo);
+        if (KAPPA) {
+            // the x face fluxes come as their difference (east minus west); the
+            // y ones are this row's north face and the previous row's
+            const V kap(G.kappa);
+            oe = fma_(kap, Cy.DX[O][0] + (Cy.FY[Q][0] - Cy.FY[O][0]), oe);
+            ou = fma_(kap, Cy.DX[O][1] + (Cy.FY[Q][1] - Cy.FY[O][1]), ou);
+            ov = fma_(kap, Cy.DX[O][2] + (Cy.FY[Q][2] - Cy.FY[O][2]), ov);
+        }
+        V ad = wetdry_fix(oe, ou, ov, cs.z, hd);
+        V spj = cfl_speed(oe, ou, ov, cs.z, G);
+        const V sum = oe + ou + ov;
+        const V dsum = sum - sum;  // NaN for a non-finite cell
+        if (edge) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                if (I.x0c + j >= nx) { ad[j] = T(0); spj[j] = T(0); }
+        }
         T added = T(0), sp = T(0);
         bool bad = false;
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-            Cell<T> cc, cx, cy;
-            cc.e = cs.e[j]; cc.u = cs.u[j]; cc.v = cs.v[j]; cc.z = cs.z[j];
-            cx.e = xs.e[j]; cx.u = xs.u[j]; cx.v = xs.v[j]; cx.z = xs.z[j];
-            cy.e = ys.e[j]; cy.u = ys.u[j]; cy.v = ys.v[j]; cy.z = ys.z[j];
-            T eo, uo, vo;
-            stage<CX, CY>(cc, cx, cy, fe[j], fw[j], fn[j], fs[j], R2.e[j], R2.u[j], R2.v[j], gn2v[j], S, hd, eo, uo,
-                          vo);
-            oe[j] = T(0.5) * (cc.e + eo);
-            ou[j] = T(0.5) * (cc.u + uo);
-            ov[j] = T(0.5) * (cc.v + vo);
-            if (KAPPA) {
-                // the x face fluxes come as their difference (east minus west); the
-                // y ones are this row's north face and the previous row's
-                oe[j] = fma_(G.kappa, Cy.DX[O][0][j] + (Cy.FY[Q][0][j] - Cy.FY[O][0][j]), oe[j]);
-                ou[j] = fma_(G.kappa, Cy.DX[O][1][j] + (Cy.FY[Q][1][j] - Cy.FY[O][1][j]), ou[j]);
-                ov[j] = fma_(G.kappa, Cy.DX[O][2][j] + (Cy.FY[Q][2][j] - Cy.FY[O][2][j]), ov[j]);
-            }
-            T ad = wetdry_fix(oe[j], ou[j], ov[j], cc.z, hd);
-            T spj = cfl_speed(oe[j], ou[j], ov[j], cc.z, G);
-            const T sum = oe[j] + ou[j] + ov[j];
-            const bool bj = !((sum - sum) == T(0));
-            if (edge && I.x0c + j >= nx) { ad = T(0); spj = T(0); }
-            added += ad;
-            sp = spj > sp ? spj : sp;
-            bad = bad || bj;
+            added += ad[j];
+            sp = spj[j] > sp ? spj[j] : sp;
+            bad = bad || !(dsum[j] == T(0));
         }
         const bool st = I.out_lane && I.x0c >= 0 && I.x0c < nx;
         ia.clamp += st ? added : T(0);
@@ -607,9 +606,9 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         if (edge) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                const T qxn = h2[j] * R2.u[j];
-                const T w = T(0.5) * (face_bnd(SIDE_W, qxn, G) + face_bnd(SIDE_W, qx[j], G));
-                const T e = T(0.5) * (face_bnd(SIDE_E, qxn, G) + face_bnd(SIDE_E, qx[j], G));
+                const T qxn0 = h2[j] * R2.u[j];
+                const T w = T(0.5) * (face_bnd(SIDE_W, qxn0, G) + face_bnd(SIDE_W, qx[j], G));
+                const T e = T(0.5) * (face_bnd(SIDE_E, qxn0, G) + face_bnd(SIDE_E, qx[j], G));
                 ia.bw += (st && I.x0c + j == 0) ? w : T(0);
                 ia.be -= (st && I.x0c + j == nx - 1) ? e : T(0);
             }
@@ -646,12 +645,9 @@ __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, 
 #pragma unroll
     for (int k = 0; k < NPRE; ++k)
         if (k < I.nr) issue_row<T, CPT>(I, k, tme, tmu, tmv, tmz);
+    Cy.NY[0] = Cy.NY[1] = Vec<T, CPT>(T(0));
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) {
-        Cy.NY[0][j] = Cy.NY[1][j] = T(0);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) Cy.FY[0][f][j] = Cy.FY[1][f][j] = Cy.DX[0][f][j] = Cy.DX[1][f][j] = T(0);
-    }
+    for (int f = 0; f < 3; ++f) Cy.FY[0][f] = Cy.FY[1][f] = Cy.DX[0][f] = Cy.DX[1][f] = Vec<T, CPT>(T(0));
     ItemAcc<T> ia;
     ia.clamp = ia.bw = ia.be = ia.bs = ia.bn = ia.smax = T(0);
     ia.bad = false;
@@ -738,10 +734,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     I.g0 = 0;
     Carry<T, CPT> Cy;
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int j = 0; j < CPT; ++j)
-            Cy.P[b].e[j] = Cy.P[b].u[j] = Cy.P[b].v[j] = Cy.P[b].z[j] = Cy.P[b].qy[j] = T(0);
+    for (int b = 0; b < 2; ++b) Cy.P[b].e = Cy.P[b].u = Cy.P[b].v = Cy.P[b].z = Cy.P[b].qy = Vec<T, CPT>(T(0));
     I.yoff = 0;
     // items from the step's queue; the next index is fetched while an item runs
     unsigned* qc = &A.ctl->qctr[A.slot_cur];
