@@ -63,15 +63,17 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def recorded_traffic():
+def recorded_traffic(rows_per_item: int):
     """DRAM bytes per launch of the fused step from the committed ncu summary,
-    valid only while the kernel sources hash to the recorded value."""
+    valid only while the kernel sources hash to the recorded value and for the
+    rows per item the capture used."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     text = open(PROFILE_SUMMARY).read()
     m = re.search(r"traffic_bytes_per_launch_8192:\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != sources_sha():
+    r = re.search(r"traffic_rows_per_item:\s*([0-9]+)", text)
+    if not m or not s or s.group(1) != sources_sha() or not r or int(r.group(1)) != rows_per_item:
         return None
     return float(m.group(1))
 
@@ -229,7 +231,7 @@ def main():
     peaks = measured_peaks()
     achieved = BYTES_PER_CELL_FP32 * cells / (launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(),
+                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(tuned_rows),
                 "peak_source": peaks["source"], "bytes_per_cell": BYTES_PER_CELL_FP32,
                 "kernel": "k_fused<float,2,...> (one launch per step)"}
 
