@@ -74,7 +74,16 @@ typedef enum { SWE_SIDE_W = 0, SWE_SIDE_E = 1, SWE_SIDE_S = 2, SWE_SIDE_N = 3 } 
 typedef enum { SWE_FP64 = 0, SWE_FP32 = 1 } swe_precision;
 typedef enum {
     SWE_KERNEL_FUSED = 0,   /* one sweep per step (default) */
-    SWE_KERNEL_PLAIN = 1    /* one thread per cell, predictor and corrector as two kernels */
+    SWE_KERNEL_PLAIN = 1,   /* one thread per cell, predictor and corrector as two kernels */
+    /* The paper's own GPU layout (Sec. 3.1), kept to measure it beside the
+     * fused sweep: one kernel per sub-step, every intermediate in global
+     * memory, one-dimensional blocks along a row.  SWE_KERNEL_PAPER computes
+     * each step size on the host from a device-to-host copy of the state
+     * (the call waits for the GPU every step); SWE_KERNEL_PAPER_DEVDT reduces
+     * it on the GPU.  With the same step sizes the state equals the other
+     * kernels' bit for bit.  No adjoint (SWE_ERR_UNSUPPORTED). */
+    SWE_KERNEL_PAPER = 2,
+    SWE_KERNEL_PAPER_DEVDT = 3
 } swe_kernel;
 
 /* Step-info flag bits */

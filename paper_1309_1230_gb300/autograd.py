@@ -20,7 +20,8 @@ class GaugeMisfit(torch.autograd.Function):
     def forward(ctx, n_field, eta0, case: dict, nsteps: int, gauges, obs, precision: int, checkpoint_every: int):
         s = swe.Solver(case["nx"], case["ny"], dx=case.get("dx", 1.0), dy=case.get("dy", 1.0),
                        manning_n=float(case.get("manning_n", 0.03)), kappa=0.0, bc=case.get("bc", (0, 0, 0, 0)),
-                       q_in=case.get("q_in", (0.0,) * 4), precision=precision)
+                       q_in=case.get("q_in", (0.0,) * 4), cfl=float(case.get("cfl", 0.5)),
+                       dt_max=float(case.get("dt_max", 10.0)), precision=precision)
         try:
             s.set_bed(case["z"], n_field.detach().double().cpu().numpy())
             s.set_state(eta0.detach().double().cpu().numpy(), case["u"], case["v"])

@@ -52,7 +52,7 @@ bool params_ok(const swe_params* p, char* why, size_t n) {
     }
     if (p->precision != SWE_FP64 && p->precision != SWE_FP32) { snprintf(why, n, "bad precision"); return false; }
     if (p->dir_cycle < 0 || p->dir_cycle > 7) { snprintf(why, n, "dir_cycle must lie in [0, 7]"); return false; }
-    if (p->kernel != SWE_KERNEL_FUSED && p->kernel != SWE_KERNEL_PLAIN) { snprintf(why, n, "bad kernel"); return false; }
+    if (p->kernel < SWE_KERNEL_FUSED || p->kernel > SWE_KERNEL_PAPER_DEVDT) { snprintf(why, n, "bad kernel"); return false; }
     if (p->seg_rows < 0 || p->seg_rows > 4096 || p->cta_warps < 0 || p->cta_warps > 16) {
         snprintf(why, n, "bad seg_rows / cta_warps"); return false;
     }
@@ -171,6 +171,7 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         if (c->h_ctl) cudaFreeHost(c->h_ctl);
         swe_fused_release(c);
+        swe_paper_release(c);
         delete c;
         return SWE_ERR_CUDA;
     };
@@ -229,6 +230,7 @@ void swe_destroy(swe_ctx* c) {
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     swe_fused_release(c);  // work plan
+    swe_paper_release(c);
     delete c;
 }
 
@@ -274,6 +276,7 @@ swe_status swe_set_bed(swe_ctx* c, const double* z, const double* n_field) {
         c->n2 = nullptr;
     }
     CK(c, cudaStreamSynchronize(c->stream));
+    swe_paper_bed_changed(c);
     c->state_set = false;  // the state must be set (and normalised) against the new bed
     return SWE_OK;
 }
@@ -284,6 +287,7 @@ swe_status swe_set_bed_device(swe_ctx* c, const void* z, const void* n_field) {
     if (!z) return fail(c, SWE_ERR_ARG, "z is NULL");
     CK(c, swe_launch_dense_copy(c, z, c->z, true));
     CK(c, swe_launch_to_double(c, c->z, c->z64));
+    swe_paper_bed_changed(c);
     if (n_field) {
         if (!c->n2) CK(c, cudaMalloc(&c->n2, c->plane * c->real_size));
         // a device n field is given as g*n^2 is not assumed: convert n -> g n^2 through FP64
@@ -417,9 +421,14 @@ swe_status swe_step(swe_ctx* c, int32_t nsteps, const double* dt_fixed, double* 
     CK(c, swe_launch_call_begin(c));
     if (c->p.kernel == SWE_KERNEL_FUSED) {
         CK(c, swe_fused_run(c, nsteps));
-    } else {
+    } else if (c->p.kernel == SWE_KERNEL_PLAIN) {
         for (int q = 0; q < nsteps; ++q) {
             CK(c, swe_launch_plain_step(c, q, c->step + q));
+            c->cur = 1 - c->cur;
+        }
+    } else {
+        for (int q = 0; q < nsteps; ++q) {
+            CK(c, swe_launch_paper_step(c, q, c->step + q));
             c->cur = 1 - c->cur;
         }
     }

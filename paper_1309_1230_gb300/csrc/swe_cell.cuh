@@ -302,12 +302,19 @@ __device__ __forceinline__ R friction(const Cell<R>& c, R gn2, T h_dry) {
 // for the predictor, predicted for the corrector); xn/yn: its neighbours in
 // the stage's one-sided directions DX/DY (ghost cells at the boundary);
 // f*: face fluxes; e0,u0,v0: the level-n values the stage updates from.
+// Continuity of one stage (S5/S11): the elevation update from the face
+// fluxes.
+template <class R, class T>
+__device__ __forceinline__ R continuity(R e0, R fe, R fw, R fn, R fs, const StepK<T>& S) {
+    return e0 - fma_(R(S.dtdx), fe - fw, R(S.dtdy) * (fn - fs));
+}
+
+// Momentum of one stage (S7/S13): advection and the wet/dry-aware pressure
+// gradient from the one-sided differences in directions DX/DY, with the
+// point-implicit friction of coefficient cf.
 template <int DX, int DY, class R, class T>
-__device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn,
-                                      R fe, R fw, R fn, R fs, R e0, R u0, R v0, R gn2,
-                                      const StepK<T>& S, T h_dry, R& eo, R& uo, R& vo) {
-    eo = e0 - fma_(R(S.dtdx), fe - fw, R(S.dtdy) * (fn - fs));
-    const R cf = friction(c, gn2, h_dry);
+__device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn, R cf, R u0, R v0,
+                                         const StepK<T>& S, T h_dry, R& uo, R& vo) {
     const R ex = eta_seen(xn, c.e, h_dry);
     const R ey = eta_seen(yn, c.e, h_dry);
     R dux, dvx, dex, duy, dvy, dey;
@@ -320,6 +327,15 @@ __device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const
     const R r = R(T(1)) / fma_(R(S.dt), cf, R(T(1)));
     uo = smul(u0 - au, r);
     vo = smul(v0 - av, r);
+}
+
+template <int DX, int DY, class R, class T>
+__device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn,
+                                      R fe, R fw, R fn, R fs, R e0, R u0, R v0, R gn2,
+                                      const StepK<T>& S, T h_dry, R& eo, R& uo, R& vo) {
+    eo = continuity(e0, fe, fw, fn, fs, S);
+    const R cf = friction(c, gn2, h_dry);
+    momentum<DX, DY>(c, xn, yn, cf, u0, v0, S, h_dry, uo, vo);
 }
 
 // Wet/dry fix (S8/S16): negative depth -> eta = z (returns the added depth),

@@ -71,6 +71,7 @@ struct swe_ctx {
     int seg_rows, seg_cols, segs_x, segs_y;
     int cta_warps;
     void* tmaps;            // device copy of the tensor maps (4 per buffer pair)
+    void* paper;            // scratch of the paper-layout step (swe_paper.cu), or NULL
     cudaGraphExec_t graph[2][6];   // cached multi-step graphs by (has dt_fixed, step % 6)
     int graph_steps[2][6];
     char err[512];
@@ -79,6 +80,9 @@ struct swe_ctx {
 // Launchers implemented in the kernel translation units; each returns the
 // launch error (cudaSuccess when queued).
 cudaError_t swe_launch_plain_step(swe_ctx* c, int s, long long k);
+cudaError_t swe_launch_paper_step(swe_ctx* c, int s, long long k);  // waits for the GPU in host-dt mode
+void swe_paper_release(swe_ctx* c);
+void swe_paper_bed_changed(swe_ctx* c);
 cudaError_t swe_launch_fused_step(swe_ctx* c, int s, long long k);
 cudaError_t swe_fused_prepare(swe_ctx* c);
 cudaError_t swe_fused_reset_flags(swe_ctx* c);

@@ -24,7 +24,7 @@ SWE_OK, SWE_ERR_ARG, SWE_ERR_CUDA, SWE_ERR_NONFINITE = 0, 1, 2, 3
 SWE_ERR_NEGDEPTH, SWE_ERR_TIMEOUT, SWE_ERR_STATE, SWE_ERR_UNSUPPORTED = 4, 5, 6, 7
 SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_OUTFLOW = 0, 1, 2
 SWE_FP64, SWE_FP32 = 0, 1
-SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN = 0, 1
+SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN, SWE_KERNEL_PAPER, SWE_KERNEL_PAPER_DEVDT = 0, 1, 2, 3
 SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED = 1, 2, 4
 SWE_NOALLOC_MAX_CELLS = 1 << 20
 
