@@ -38,22 +38,31 @@ def gauge_series(case: dict, n_field, nsteps: int, gauges, precision: int = swe.
 
 def calibrate_manning(case: dict, gauges, obs, nsteps: int, n_init, iters: int = 20, smooth: float = 0.0,
                       precision: int = swe.SWE_FP64, device: str = "cpu"):
-    """Returns (n_field, history of the loss at each evaluation)."""
+    """Returns (n_field, history of the objective at each evaluation).  The
+    optimiser sees the objective divided by its starting value, so that its
+    stopping tolerances do not depend on the scale of the records."""
     theta = torch.tensor(np.log(np.asarray(n_init, dtype=np.float64)), device=device, requires_grad=True)
     eta0 = torch.tensor(np.asarray(case["eta"], dtype=np.float64), device=device)
     opt = torch.optim.LBFGS([theta], lr=1.0, max_iter=int(iters), history_size=10,
-                            line_search_fn="strong_wolfe", tolerance_grad=1e-12, tolerance_change=1e-14)
+                            line_search_fn="strong_wolfe", tolerance_grad=1e-10, tolerance_change=1e-14)
     history = []
+    scale = []
 
-    def closure():
-        opt.zero_grad()
+    def objective():
         n = torch.exp(theta)
         loss = gauge_misfit(n, eta0, case, nsteps, gauges, obs, precision)
         if smooth > 0.0:
             loss = loss + smooth * (torch.sum(torch.diff(theta, dim=0) ** 2) + torch.sum(torch.diff(theta, dim=1) ** 2))
-        loss.backward()
-        history.append(float(loss.detach()))
         return loss
+
+    def closure():
+        opt.zero_grad()
+        loss = objective()
+        history.append(float(loss.detach()))
+        if not scale:
+            scale.append(1.0 / history[0] if history[0] > 0 else 1.0)
+        (loss * scale[0]).backward()
+        return loss * scale[0]
 
     opt.step(closure)
     return torch.exp(theta).detach().cpu().numpy(), history

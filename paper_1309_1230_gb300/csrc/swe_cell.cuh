@@ -238,8 +238,17 @@ struct vecn<float, 2> {
     friend __device__ __forceinline__ vecn pow_m43(vecn a) { return vecn(pow_m43(a.v.x), pow_m43(a.v.y)); }
 };
 
-template <class R>
-__device__ __forceinline__ R tmax(R a, R b) { return sel(a > b, a, b); }
+// Maximum of two switch values or speeds (never NaN in a finite state; a
+// non-finite state is flagged separately).
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+template <class T, int N>
+__device__ __forceinline__ vecn<T, N> tmax(vecn<T, N> a, vecn<T, N> b) {
+    vecn<T, N> r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = tmax(a[i], b[i]);
+    return r;
+}
 
 // Elevation of neighbour nb seen by the pressure term of a cell at elevation
 // eta_self: a dry neighbour whose bed is above eta_self acts as a wall.
@@ -292,8 +301,8 @@ __device__ __forceinline__ void faces(T qc, T qn, bool lo, bool hi, int side_lo,
 template <class R, class T>
 __device__ __forceinline__ R friction(const Cell<R>& c, R gn2, T h_dry) {
     const R h = c.e - c.z;
-    const R s2 = fma_(c.u, c.u, c.v * c.v);
-    const R mag = sel(s2 > R(0), rsq_sqrt(s2), R(0));
+    const R s2 = fma_(c.u, c.u, c.v * c.v);  // >= +0, and sqrt(+0) = +0
+    const R mag = rsq_sqrt(s2);
     return sel(h > R(h_dry), gn2 * mag * pow_m43(h), R(0));
 }
 
@@ -342,34 +351,34 @@ __device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const
 // dry -> zero velocity.
 template <class R, class T>
 __device__ __forceinline__ R wetdry_fix(R& e, R& u, R& v, R z, T h_dry) {
-    R h = e - z;
+    const R h = e - z;
     const auto neg = h < R(T(0));
     const R added = sel(neg, z - e, R(T(0)));  // -h, exactly
     e = sel(neg, z, e);
-    h = sel(neg, R(T(0)), h);
-    const auto dry = h <= R(h_dry);
+    const auto dry = h <= R(h_dry);            // includes h < 0 (h_dry > 0)
     u = sel(dry, R(T(0)), u);
     v = sel(dry, R(T(0)), v);
     return added;
 }
 
 // Dissipation switch of a cell along one axis (S15).
-__device__ __forceinline__ float nu_switch(float hl, float hc, float hr) {
-    const float num = fabsf(fma_(-2.0f, hc, hl + hr));
-    const float den = fma_(2.0f, fabsf(hc), fabsf(hl) + fabsf(hr)) + (float)SWE_NU_TINY;
-    return num / den;
-}
-__device__ __forceinline__ double nu_switch(double hl, double hc, double hr) {
-    const double num = fabs(fma_(-2.0, hc, hl + hr));
-    const double den = fma_(2.0, fabs(hc), fabs(hl) + fabs(hr)) + SWE_NU_TINY;
-    return num / den;
-}
-template <class T, int N>  // per cell: the absolute values fold into the scalar instructions
-__device__ __forceinline__ vecn<T, N> nu_switch(vecn<T, N> hl, vecn<T, N> hc, vecn<T, N> hr) {
+// The depths are never negative (the wet/dry fix keeps eta >= z, ghost
+// cells copy an interior depth), so |h| = h in the denominator.
+__device__ __forceinline__ float absv(float x) { return fabsf(x); }
+__device__ __forceinline__ double absv(double x) { return fabs(x); }
+template <class T, int N>
+__device__ __forceinline__ vecn<T, N> absv(vecn<T, N> x) {
     vecn<T, N> r;
 #pragma unroll
-    for (int i = 0; i < N; ++i) r[i] = nu_switch(hl[i], hc[i], hr[i]);
+    for (int i = 0; i < N; ++i) r[i] = absv(x[i]);
     return r;
+}
+template <class R>
+__device__ __forceinline__ R nu_switch(R hl, R hc, R hr) {
+    const R s = hl + hr;
+    const R num = absv(fma_(R(-2.0f), hc, s));
+    const R den = fma_(R(2.0f), hc, s) + R(SWE_NU_TINY);
+    return num / den;
 }
 
 // Face coefficient of the dissipation: interior face between two wet cells.

@@ -167,7 +167,7 @@ def test_calibration_recovers_the_gauge_records():
     obs = C.gauge_series(c, c["n_true"], T, c["gauges"])
     n0 = np.full_like(c["n_true"], 0.03)
     loss0 = float(np.sum((C.gauge_series(c, n0, T, c["gauges"]) - obs) ** 2) / 2)
-    n_fit, hist = C.calibrate_manning(c, c["gauges"], obs, T, n0, iters=15, smooth=1e-6)
+    n_fit, hist = C.calibrate_manning(c, c["gauges"], obs, T, n0, iters=20)
     assert hist[0] == pytest.approx(loss0, rel=1e-9)
     assert min(hist) <= 0.1 * hist[0], hist[:3] + hist[-3:]
     assert np.all(n_fit > 0)
