@@ -212,6 +212,30 @@ int32_t swe_autotune_candidates(swe_ctx* ctx, int32_t* rows, int32_t cap);
 swe_status swe_autotune(swe_ctx* ctx, int32_t probe_steps, const int32_t* rows, int32_t nrows, double* ms_per_step,
                         int32_t* chosen);
 
+/* ---------------------------------------------------------------- strips
+ * Row-strip decomposition of one domain over several contexts (Sec. 6.1 of
+ * the paper proposes it for several GPUs): each strip context holds its own
+ * rows plus two halo rows on every side that faces another strip.  One step
+ * of the decomposed domain is: swe_step(strip, 1, ...) on every strip, then
+ * swe_copy_rows for every halo (from the neighbour's current level), then
+ * swe_cfl_combine over all strips.  Call swe_cfl_combine once after the
+ * states are set, too.  The own rows then equal the undecomposed domain's
+ * bit for bit, step sizes included.
+ *
+ * swe_set_own_rows marks rows [lo, hi) as the context's own (default: all
+ * rows): halo rows are stepped like the others but enter no tally, no CFL
+ * maximum and no diagnostic of swe_get_info.  swe_copy_rows copies nrows rows
+ * of the current level (eta, u, v) of src from its row src_row into dst from
+ * row dst_row (same nx, precision and device), ordered after the work queued
+ * on both contexts, and clears dst's dry-skip flags.  swe_cfl_combine
+ * replaces the CFL maximum of every context's current level by the maximum
+ * over the n contexts (same step index, same device; n <= 64).  The sides
+ * that face another strip may have any boundary condition: it only touches
+ * halo rows. */
+swe_status swe_set_own_rows(swe_ctx* ctx, int32_t lo, int32_t hi);
+swe_status swe_copy_rows(swe_ctx* dst, int32_t dst_row, const swe_ctx* src, int32_t src_row, int32_t nrows);
+swe_status swe_cfl_combine(swe_ctx* const* ctxs, int32_t n);
+
 /* ---------------------------------------------------------------- batches
  * Many independent scenarios of uneven grid size advanced together (FP32),
  * each with its own CFL step: one persistent cooperative launch per

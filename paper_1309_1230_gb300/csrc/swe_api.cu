@@ -211,6 +211,8 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
     if ((e = cudaMalloc(&c->bad_flag, sizeof(unsigned int))) != cudaSuccess) return bail(e, "cudaMalloc");
     c->cur = 0;
     c->step = 0;
+    c->own_lo = 0;
+    c->own_hi = p->ny;
     // the set-up memsets ran on the legacy default stream, which the
     // context's non-blocking stream does not wait for
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "cudaDeviceSynchronize");

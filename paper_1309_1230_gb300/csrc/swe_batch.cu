@@ -418,6 +418,7 @@ BatchArgs make_args(const swe_batch* b, int nsteps) {
     memset(&B, 0, sizeof(B));
     const swe_params& p = b->p;
     B.G.nx = 0; B.G.ny = 0; B.G.pitch = b->pitch;
+    B.G.own_lo = 0; B.G.own_hi = 1 << 30;  // every row of a scenario is its own
     B.G.g = (T)p.g; B.G.h_dry = (T)p.h_dry; B.G.kappa = (T)p.kappa; B.G.gn2 = 0.f;
     B.G.inv_dx = (T)(1.0 / p.dx); B.G.inv_dy = (T)(1.0 / p.dy);
     for (int s = 0; s < 4; ++s) {

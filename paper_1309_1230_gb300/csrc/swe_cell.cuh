@@ -45,6 +45,10 @@ struct GridK {
     T inv_dx, inv_dy;        // for the CFL speed
     T qin[4];                // inflow discharge into the domain per side
     int bc[4];
+    // Rows [own_lo, own_hi) are the grid's own; the others are halo rows
+    // copied from a neighbouring strip of a decomposed domain: they are
+    // stepped like any row but enter no tally and no CFL maximum.
+    int own_lo = 0, own_hi = 1 << 30;
 };
 
 // Step constants, rounded from the FP64 step size.

@@ -445,7 +445,8 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         P.e = eo; P.u = uo; P.v = vo; P.z = c.z;
         P.qy = (eo - c.z) * vo;
         // a predicted clamp counts once per cell: in the item and lane that output it
-        if (I.out_lane && p >= I.y0 && p < I.y1 && I.x0c >= 0) ia.clamp = fma_(T(0.5), added, ia.clamp);
+        if (I.out_lane && p >= I.y0 && p < I.y1 && I.x0c >= 0 && p >= G.own_lo && p < G.own_hi)
+            ia.clamp = fma_(T(0.5), added, ia.clamp);
 
         if (KAPPA) {
             // x dissipation of row r-1: the other side's neighbours need no halo
@@ -594,9 +595,10 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             bad = bad || !(dsum[j] == T(0));
         }
         const bool st = I.out_lane && I.x0c >= 0 && I.x0c < nx;
-        ia.clamp += st ? added : T(0);
-        ia.smax = (st && sp > ia.smax) ? sp : ia.smax;
-        ia.bad = ia.bad || (st && bad);
+        const bool own = st && C >= G.own_lo && C < G.own_hi;  // halo rows of a strip: stored, not tallied
+        ia.clamp += own ? added : T(0);
+        ia.smax = (own && sp > ia.smax) ? sp : ia.smax;
+        ia.bad = ia.bad || (own && bad);
         if (st) {
             const size_t o = (size_t)C * G.pitch + I.x0c;
             st_vec<T, CPT>(A.e1 + o, oe);
@@ -609,14 +611,14 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 const T qxn0 = h2[j] * R2.u[j];
                 const T w = T(0.5) * (face_bnd(SIDE_W, qxn0, G) + face_bnd(SIDE_W, qx[j], G));
                 const T e = T(0.5) * (face_bnd(SIDE_E, qxn0, G) + face_bnd(SIDE_E, qx[j], G));
-                ia.bw += (st && I.x0c + j == 0) ? w : T(0);
-                ia.be -= (st && I.x0c + j == nx - 1) ? e : T(0);
+                ia.bw += (own && I.x0c + j == 0) ? w : T(0);
+                ia.be -= (own && I.x0c + j == nx - 1) ? e : T(0);
             }
         }
         if (brow && (C == 0 || C == ny - 1)) {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                const bool in = st && !(edge && I.x0c + j >= nx);
+                const bool in = own && !(edge && I.x0c + j >= nx);
                 const T qyn = h2[j] * R2.v[j];
                 const T sv = T(0.5) * (face_bnd(SIDE_S, qyn, G) + face_bnd(SIDE_S, pc.qy[j], G));
                 const T nv = T(0.5) * (face_bnd(SIDE_N, qyn, G) + face_bnd(SIDE_N, pc.qy[j], G));
@@ -840,6 +842,7 @@ cudaError_t launch_t(swe_ctx* c, const Plan& pl, int s, long long k) {
     A.G.gn2 = (T)(p.g * p.manning_n * p.manning_n);
     A.G.inv_dx = (T)(1.0 / p.dx); A.G.inv_dy = (T)(1.0 / p.dy);
     for (int q = 0; q < 4; ++q) { A.G.bc[q] = p.bc[q]; A.G.qin[q] = (T)p.q_in[q]; }
+    A.G.own_lo = c->own_lo; A.G.own_hi = c->own_hi;
     const int a = c->cur, b = 1 - c->cur;
     A.e1 = (T*)c->eta[b]; A.u1 = (T*)c->u[b]; A.v1 = (T*)c->v[b];
     A.n2 = (const T*)c->n2;

@@ -72,6 +72,7 @@ struct swe_ctx {
     int cta_warps;
     void* tmaps;            // device copy of the tensor maps (4 per buffer pair)
     void* paper;            // scratch of the paper-layout step (swe_paper.cu), or NULL
+    int own_lo, own_hi;     // own rows of a strip of a decomposed domain (default all rows)
     cudaGraphExec_t graph[2][6];   // cached multi-step graphs by (has dt_fixed, step % 6)
     int graph_steps[2][6];
     char err[512];

@@ -86,8 +86,10 @@ __global__ void k_prologue(GridK<T> G, const T* e, const T* u, const T* v, const
     size_t n = (size_t)G.nx * G.ny;
     T m = T(0);
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        size_t k = (q / G.nx) * (size_t)G.pitch + q % G.nx;
+        const int row = (int)(q / G.nx);
+        size_t k = (size_t)row * G.pitch + q % G.nx;
         T s = cfl_speed(e[k], u[k], v[k], z[k], G);
+        if (row < G.own_lo || row >= G.own_hi) s = T(0);
         m = s > m ? s : m;
     }
     m = warp_max(m);
@@ -106,7 +108,8 @@ __global__ void k_diag_part(GridK<T> G, const T* e, const T* u, const T* v, cons
     double s = 0.0;
     long long w = 0;
     unsigned int b = 0;
-    for (int j = j0; j < j1; ++j)
+    for (int j = j0; j < j1; ++j) {
+        if (j < G.own_lo || j >= G.own_hi) continue;  // halo rows of a strip
         for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
             size_t k = (size_t)j * G.pitch + i;
             double h = (double)e[k] - (double)z[k];
@@ -114,6 +117,7 @@ __global__ void k_diag_part(GridK<T> G, const T* e, const T* u, const T* v, cons
             w += (T)(e[k] - z[k]) > G.h_dry;
             if (!isfinite(e[k]) || !isfinite(u[k]) || !isfinite(v[k])) b = 1;
         }
+    }
     s = warp_sum(s);
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __
         stage<SX, SY>(c, xn, yn, fe, fw, fn, fs, c.e, c.u, c.v, gn2, S, G.h_dry, eo, uo, vo);
         added = wetdry_fix(eo, uo, vo, c.z, G.h_dry);
         es[k] = eo; us[k] = uo; vs[k] = vo;
+        if (j < G.own_lo || j >= G.own_hi) added = T(0);
     }
     // predictor clamps count half (the average keeps half of the predicted level)
     if (__any_sync(0xffffffffu, added != T(0))) {
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, con
         if (i == G.nx - 1) be = -0.5 * ((double)face_bnd(SIDE_E, qxn, G) + (double)face_bnd(SIDE_E, qxs, G));
         if (j == 0) bs = 0.5 * ((double)face_bnd(SIDE_S, qyn, G) + (double)face_bnd(SIDE_S, qys, G));
         if (j == G.ny - 1) bn = -0.5 * ((double)face_bnd(SIDE_N, qyn, G) + (double)face_bnd(SIDE_N, qys, G));
+        if (j < G.own_lo || j >= G.own_hi) { added = T(0); speed = T(0); bad = false; bw = be = bs = bn = 0.0; }
     }
     const int lane = threadIdx.x & 31;
     T m = warp_max(speed);
@@ -192,6 +194,7 @@ static GridK<T> grid_of(const swe_ctx* c) {
     G.gn2 = (T)(p.g * p.manning_n * p.manning_n);
     G.inv_dx = (T)(1.0 / p.dx); G.inv_dy = (T)(1.0 / p.dy);
     for (int s = 0; s < 4; ++s) { G.bc[s] = p.bc[s]; G.qin[s] = (T)p.q_in[s]; }
+    G.own_lo = c->own_lo; G.own_hi = c->own_hi;
     return G;
 }
 

@@ -93,6 +93,9 @@ _SIGS = {
     "swe_batch_last_error": (ctypes.c_char_p, [_vp]),
     "swe_adjoint": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _dp,
                                    ctypes.c_int32, _dp, _dp, _dp]),
+    "swe_set_own_rows": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.c_int32]),
+    "swe_copy_rows": (ctypes.c_int, [_ctxp, ctypes.c_int32, _ctxp, ctypes.c_int32, ctypes.c_int32]),
+    "swe_cfl_combine": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]),
     "swe_autotune_candidates": (ctypes.c_int32, [_ctxp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "swe_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _dp,
                                     ctypes.POINTER(ctypes.c_int32)]),
@@ -271,6 +274,14 @@ class Solver:
         _check(st, self.ctx)
         return float(loss[0]), gn, ge
 
+    def set_own_rows(self, lo: int, hi: int):
+        """Rows [lo, hi) are this strip's own; the rest are halo rows."""
+        _check(self.lib.swe_set_own_rows(self.ctx, int(lo), int(hi)), self.ctx)
+
+    def copy_rows_from(self, src: "Solver", src_row: int, dst_row: int, nrows: int):
+        """Copies nrows rows of src's current level into this context."""
+        _check(self.lib.swe_copy_rows(self.ctx, int(dst_row), src.ctx, int(src_row), int(nrows)), self.ctx)
+
     def autotune(self, probe_steps: int = 10, rows=None):
         """Times each candidate rows-per-item of the fused step on the current
         state (which is restored) and keeps the fastest; returns (chosen,
@@ -301,6 +312,13 @@ class Solver:
 
     def stream_handle(self) -> int:
         return int(self.lib.swe_stream(self.ctx) or 0)
+
+
+def cfl_combine(solvers):
+    """Gives every strip the CFL maximum over all of them (swe_cfl_combine)."""
+    arr = (ctypes.c_void_p * len(solvers))(*[x.ctx.value for x in solvers])
+    st = load().swe_cfl_combine(arr, len(solvers))
+    _check(st, solvers[0].ctx)
 
 
 def _torch_check(a, s: Solver):
@@ -359,6 +377,14 @@ class Batch:
         infos = (swe_step_info * self.count)() if want_info else None
         self._chk(self.lib.swe_batch_step(self.b, int(nsteps), infos))
         return [_info(x) for x in infos] if want_info else None
+
+    def set_own_rows(self, lo: int, hi: int):
+        """Rows [lo, hi) are this strip's own; the rest are halo rows."""
+        _check(self.lib.swe_set_own_rows(self.ctx, int(lo), int(hi)), self.ctx)
+
+    def copy_rows_from(self, src: "Solver", src_row: int, dst_row: int, nrows: int):
+        """Copies nrows rows of src's current level into this context."""
+        _check(self.lib.swe_copy_rows(self.ctx, int(dst_row), src.ctx, int(src_row), int(nrows)), self.ctx)
 
     def autotune(self, probe_steps: int = 10, rows=None):
         """Times each candidate rows-per-item on the current states (which are
