@@ -70,10 +70,9 @@ def recorded_traffic(rows_per_item: int):
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     text = open(PROFILE_SUMMARY).read()
-    m = re.search(r"traffic_bytes_per_launch_8192:\s*([0-9.eE+]+)", text)
+    m = re.search(r"traffic_bytes_per_launch_8192_rows%d:\s*([0-9.eE+]+)" % rows_per_item, text)
     s = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", text)
-    r = re.search(r"traffic_rows_per_item:\s*([0-9]+)", text)
-    if not m or not s or s.group(1) != sources_sha() or not r or int(r.group(1)) != rows_per_item:
+    if not m or not s or s.group(1) != sources_sha():
         return None
     return float(m.group(1))
 
