@@ -156,3 +156,30 @@ def adjoint_case(nx: int = 512, ny: int = 512, seed: int = 1313, n_gauges: int =
     return dict(nx=nx, ny=ny, dx=1.0, dy=1.0, z=z, eta=eta, u=np.zeros_like(z),
                 v=np.zeros_like(z), manning_n=n0, kappa=0.0, n_true=n_true,
                 bc=(WALL, WALL, WALL, WALL), q_in=(0.0, 0.0, 0.0, 0.0), gauges=gauges)
+
+
+def large_river(nx: int, ny: int, seed: int = 1314, chunk_rows: int = 2048) -> dict:
+    """A river reach too large for the filtered-noise generator: bed sloping
+    1e-3 along x plus three seeded sinusoidal undulations (0.3, 0.1 and
+    0.05 m), depth 1 m plus a 0.05 m long wave, u = 0.1 sin(.), v = 0; inflow
+    2 m^2/s west, outflow east, walls south/north, n = 0.03, kappa = 0.25.
+    Arrays are FP32 (ny x nx), built row block by row block to bound the
+    host memory; the same seed gives the same arrays."""
+    rng = _rng(seed)
+    ph = rng.uniform(0.0, 2.0 * np.pi, 6)
+    shape = (ny, nx)
+    z = np.empty(shape, np.float32)
+    eta = np.empty(shape, np.float32)
+    u = np.empty(shape, np.float32)
+    v = np.zeros(shape, np.float32)
+    x = (np.arange(nx) + 0.5)[None, :]
+    for j0 in range(0, ny, chunk_rows):
+        j1 = min(ny, j0 + chunk_rows)
+        y = (np.arange(j0, j1) + 0.5)[:, None]
+        zz = (-1e-3 * x + 0.3 * np.sin(2 * np.pi * x / 1500.0 + ph[0]) * np.sin(2 * np.pi * y / 900.0 + ph[1])
+              + 0.1 * np.sin(2 * np.pi * (x + y) / 377.0 + ph[2]) + 0.05 * np.sin(2 * np.pi * (x - y) / 131.0 + ph[3]))
+        z[j0:j1] = zz
+        eta[j0:j1] = zz + 1.0 + 0.05 * np.sin(2 * np.pi * x / 2000.0 + ph[4])
+        u[j0:j1] = 0.1 * np.sin(2 * np.pi * y / 700.0 + ph[5]) + 0.0 * x
+    return dict(nx=nx, ny=ny, dx=1.0, dy=1.0, z=z, eta=eta, u=u, v=v, manning_n=0.03, kappa=0.25,
+                bc=(INFLOW, OUTFLOW, WALL, WALL), q_in=(2.0, 0.0, 0.0, 0.0))

@@ -300,6 +300,12 @@ class Solver:
         return int(chosen.value), dict(zip([int(r) for r in rows], ms.tolist()))
 
     # torch tensors on the context's device, of the context's real type
+    def set_bed_device(self, z, n_field=None):
+        for a in (z,) + ((n_field,) if n_field is not None else ()):
+            _torch_check(a, self)
+        _check(self.lib.swe_set_bed_device(self.ctx, z.data_ptr(), n_field.data_ptr() if n_field is not None else None),
+               self.ctx)
+
     def set_state_device(self, eta, u, v):
         for a in (eta, u, v):
             _torch_check(a, self)
