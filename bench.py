@@ -146,6 +146,27 @@ def oracle_rate(case, nsteps: int, crop: int, threads: int):
     return crop * crop * nsteps / dt, dt
 
 
+def slowest_rank_ms(local_ms: float, dist=None) -> float:
+    """The largest per-rank duration (ms): the job takes as long as its slowest
+    replica.  Single process when dist is None or not initialised."""
+    if dist is None or not dist.is_initialized():
+        return local_ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank: int, steps: int, local_ms: float, dist=None):
+    """Whole-job cell-updates/s: the cells every rank advanced (weak scaling,
+    one replica of the workload per rank) over the slowest rank's time;
+    returns (rate, that time in ms)."""
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    ms = slowest_rank_ms(local_ms, dist)
+    return world * cells_per_rank * steps / (ms / 1e3), ms
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -219,13 +240,8 @@ def main():
         s.step(args.steps, want_info=False)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = job_rate(cells, args.steps, ev0.elapsed_time(ev1), dist)
     info = s.info()
-    value = world * cells * args.steps / (ms / 1e3)
     launch_ms = ms / args.steps  # one fused kernel per step (plus one tiny bookkeeping kernel per call)
     peaks = measured_peaks()
     achieved = BYTES_PER_CELL_FP32 * cells / (launch_ms / 1e3) / 1e9
@@ -250,14 +266,10 @@ def main():
         st |= lib.swe_step(s.ctx, args.steps, None, None, None)
         st |= lib.swe_get_state(s.ctx, ptr[3], ptr[4], ptr[5])
         torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([secs], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
+        e2e_rate, _ = job_rate(cells, args.steps, (time.perf_counter() - t0) * 1e3, dist)
         assert st == 0, "e2e C-ABI calls failed"
         io_bytes = 3 * 8 * cells
-        e2e = {"value": world * cells * args.steps / secs, "unit": METRIC,
+        e2e = {"value": e2e_rate, "unit": METRIC,
                "h2d_bytes_per_step": io_bytes / args.steps, "d2h_bytes_per_step": io_bytes / args.steps,
                "calls": "swe_set_state(host f64) + swe_step(K) + swe_get_state(host f64), pinned buffers"}
         if not np.isfinite(pin[3].numpy()).all():
