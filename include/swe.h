@@ -258,7 +258,7 @@ swe_status swe_batch_set_state(swe_batch* b, int32_t idx, const double* eta, con
 swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos);
 swe_status swe_batch_get_state(swe_batch* b, int32_t idx, double* eta, double* u, double* v);
 /* Work-item autotuner of the batched step, as swe_autotune: the built-in
- * candidates are 16 to 192 rows per item; the probes run on the batch's
+ * candidates are 32 to 512 rows per item (default 192); the probes run on the batch's
  * current states, which are restored with their clocks and tallies (the
  * dry-skip flags are cleared).  The items are rebuilt for the chosen height,
  * which also becomes the batch's seg_rows. */

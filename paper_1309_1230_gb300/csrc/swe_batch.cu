@@ -99,6 +99,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
             }
         }
         __threadfence();
+        // the next step's TMA loads (async proxy) read rows other CTAs stored
+        // with ordinary stores (generic proxy)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
     return ok != 0;
@@ -175,14 +178,14 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int qx = bi.kx + dx, qy = bi.ky + dy;
                     if (qx < 0 || qy < 0 || qx >= sc.nxs || qy >= sc.nys) continue;
-                    dry = dry && !(fl_in[sc.item0 + qy * sc.nxs + qx] & 1u);
+                    dry = dry && !(__ldcg(fl_in + sc.item0 + qy * sc.nxs + qx) & 1u);  // written by other SMs
                 }
             const bool touches_inflow = (B.inflow_side[SIDE_W] && bi.kx == 0) ||
                                         (B.inflow_side[SIDE_E] && bi.kx == sc.nxs - 1) ||
                                         (B.inflow_side[SIDE_S] && bi.ky == 0) ||
                                         (B.inflow_side[SIDE_N] && bi.ky == sc.nys - 1);
             dry = dry && !touches_inflow;
-            if (B.dry_skip && dry && (fl_in[bi.fi] & 2u)) {
+            if (B.dry_skip && dry && (__ldcg(fl_in + bi.fi) & 2u)) {
                 if (lane == 0) fl_out[bi.fi] = 2u;
                 continue;
             }
@@ -561,7 +564,7 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
     for (int s = 0; s < count; ++s) { b->row0[s] = (int)r; r += ny[s]; }
     b->rows = r;
     b->plane = (size_t)b->pitch * (size_t)b->rows;
-    b->L = p->seg_rows > 0 ? p->seg_rows : 64;
+    b->L = p->seg_rows > 0 ? p->seg_rows : 192;
     auto bail = [&](const char* what, cudaError_t e) {
         fprintf(stderr, "swe_batch_create: %s: %s\n", what, cudaGetErrorString(e));
         free_batch(b);
@@ -778,7 +781,7 @@ swe_status swe_batch_get_state(swe_batch* b, int32_t idx, double* eta, double* u
 }
 
 // Built-in candidate rows per item of the batched step.
-static const int kBatchRows[] = {16, 24, 32, 48, 64, 96, 128, 192};
+static const int kBatchRows[] = {32, 64, 96, 128, 192, 256, 384, 512};
 
 int32_t swe_batch_autotune_candidates(swe_batch* b, int32_t* rows, int32_t cap) {
     swe_status s = check_batch(b);
