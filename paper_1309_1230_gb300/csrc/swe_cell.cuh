@@ -87,6 +87,19 @@ __device__ __forceinline__ double pow_m43(double h) {
 __device__ __forceinline__ float rsq_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double rsq_sqrt(double x) { return sqrt(x); }
 
+// Reciprocal and quotient.  FP32: the hardware reciprocal (PTX rcp.approx,
+// about 1 ulp) times the numerator, with no range scaling: the denominators
+// here (a friction factor >= 1, a switch denominator of depths plus
+// SWE_NU_TINY) stay far inside the normal FP32 range.  FP64: IEEE division.
+__device__ __forceinline__ float rcp_(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+
 template <class T>
 __device__ __forceinline__ T sel(bool c, T a, T b) { return c ? a : b; }
 
@@ -175,6 +188,18 @@ struct vecn {
         for (int i = 0; i < N; ++i) r.c[i] = m.c[i] ? a.c[i] : b.c[i];
         return r;
     }
+    friend __device__ __forceinline__ vecn rcp_(vecn a) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = rcp_(a.c[i]);
+        return r;
+    }
+    friend __device__ __forceinline__ vecn div_(vecn a, vecn b) {
+        vecn r;
+#pragma unroll
+        for (int i = 0; i < N; ++i) r.c[i] = div_(a.c[i], b.c[i]);
+        return r;
+    }
     friend __device__ __forceinline__ vecn rsq_sqrt(vecn a) {
         vecn r;
 #pragma unroll
@@ -239,6 +264,8 @@ struct vecn<float, 2> {
         return vecn(m.c[0] ? a.v.x : b.v.x, m.c[1] ? a.v.y : b.v.y);
     }
     friend __device__ __forceinline__ vecn rsq_sqrt(vecn a) { return vecn(sqrtf(a.v.x), sqrtf(a.v.y)); }
+    friend __device__ __forceinline__ vecn rcp_(vecn a) { return vecn(rcp_(a.v.x), rcp_(a.v.y)); }
+    friend __device__ __forceinline__ vecn div_(vecn a, vecn b) { return a * vecn(rcp_(b.v.x), rcp_(b.v.y)); }
     friend __device__ __forceinline__ vecn pow_m43(vecn a) { return vecn(pow_m43(a.v.x), pow_m43(a.v.y)); }
 };
 
@@ -337,7 +364,7 @@ __device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, co
     else        { duy = c.u - yn.u; dvy = c.v - yn.v; dey = c.e - ey; }
     const R au = fma_(c.u, R(S.dtdx) * dux, fma_(c.v, R(S.dtdy) * duy, R(S.g_dtdx) * dex));
     const R av = fma_(c.u, R(S.dtdx) * dvx, fma_(c.v, R(S.dtdy) * dvy, R(S.g_dtdy) * dey));
-    const R r = R(T(1)) / fma_(R(S.dt), cf, R(T(1)));
+    const R r = rcp_(fma_(R(S.dt), cf, R(T(1))));
     uo = smul(u0 - au, r);
     vo = smul(v0 - av, r);
 }
@@ -382,7 +409,7 @@ __device__ __forceinline__ R nu_switch(R hl, R hc, R hr) {
     const R s = hl + hr;
     const R num = absv(fma_(R(-2.0f), hc, s));
     const R den = fma_(R(2.0f), hc, s) + R(SWE_NU_TINY);
-    return num / den;
+    return div_(num, den);
 }
 
 // Face coefficient of the dissipation: interior face between two wet cells.
@@ -396,11 +423,13 @@ template <class T>
 __device__ __forceinline__ T dflux(T eps, T hi, T lo) { return eps * (hi - lo); }
 
 // S15 for one field of a cell from its four face fluxes (east, west, north,
-// south): out + kappa * ((fe - fw) + (fn - fs)).  Every kernel form builds the
-// same face fluxes with dflux, so a face is rounded the same from both sides.
+// south): out + kappa * (((fe - fw) - fs) + fn).  Every kernel form builds the
+// same face fluxes with dflux, so a face is rounded the same from both sides,
+// and sums them in this order (the fused sweep carries east - west - south
+// from one row to the next and adds the north face when it arrives).
 template <class R, class T>
 __device__ __forceinline__ R dissip_faces(R out, R fe, R fw, R fn, R fs, T kappa) {
-    return fma_(R(kappa), (fe - fw) + (fn - fs), out);
+    return fma_(R(kappa), ((fe - fw) - fs) + fn, out);
 }
 
 // CFL speed of a cell (S2); 0 for dry cells.

@@ -20,9 +20,10 @@
 // mbarrier), NPRE rows ahead of use; a row stays in the ring while any of the
 // four rows of the step's stencil window still needs it.  The two predicted
 // rows and the y dissipation switches the corrector needs are carried in
-// registers from one row to the next.  x neighbours come from adjacent lanes
-// by shuffles; the strip's output-side edge lane reads the ring's halo
-// columns (the other edge lane never outputs).  Boundary handling runs under
+// registers from one row to the next.  The level-n x neighbours outside a
+// lane's cells are read from the ring (its columns extend two cells beyond
+// the strip on both sides); the predicted ones come from adjacent lanes by
+// shuffles (the lane that would need a halo there never outputs).  Boundary handling runs under
 // warp-uniform branches: per row for the y sides, per item for the x sides.  The new level is stored with
 // 16-byte vector stores.  Out-of-grid rows and columns read as zeros (TMA
 // fill) and are replaced by the ghost cells of the boundary conditions.
@@ -57,7 +58,9 @@ struct Geo {
     static constexpr int FSTRIDE = ((BW * (int)sizeof(T) + 127) / 128) * 128;  // bytes per field row
     static constexpr int SLOT = 4 * FSTRIDE;              // bytes per ring slot (eta, u, v, z)
     static constexpr int WARP_SMEM = NSLOT * SLOT;
-    static constexpr int MINB = (sizeof(T) == 4 && CPT <= 2) ? 16 : 8;  // CTAs per SM the registers must allow
+    // CTAs per SM the register budget must allow (FP32: 15 leaves the compiler
+    // 136 registers; it uses at most 128, so 16 CTAs still fit)
+    static constexpr int MINB = (sizeof(T) == 4 && CPT <= 2) ? 15 : 8;
 };
 
 // What one work item reads and writes: its scenario's constants and the
@@ -189,8 +192,9 @@ template <class T, int CPT>
 struct Carry {
     PR<T, CPT> P[2];         // predicted rows
     Vec<T, CPT> NY[2];       // y dissipation switch of a level-n row
-    Vec<T, CPT> FY[2][3];    // y dissipation face flux (eta, u, v) above a row
-    Vec<T, CPT> DX[2][3];    // x dissipation (east minus west face flux) of a row
+    // S15 dissipation of a row (eta, u, v) without its north face flux: east
+    // minus west, minus south (the south face is the previous row's north face)
+    Vec<T, CPT> DX[2][3];
 };
 
 struct Acc {  // per-warp totals over its items, FP64
@@ -329,9 +333,11 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     const int lane = I.lane;
     const int r = I.y0 - 2 + k;
 
-    fence_async_smem();  // ring row k-4 (read last iteration) is refilled next
-    if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
-    if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
+    if (GEN) {  // the lean rows come in pairs, loaded and waited for by the caller
+        fence_async_smem();  // ring row k-4 (read two rows ago) is refilled next
+        if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
+        if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
+    }
     if (GEN && k < 2) return;
 
     // -------- level-n rows r, r-1, r-2 (ghost cells outside [0, ny)).  The
@@ -359,15 +365,17 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     }
     const V h0 = R0.e - R0.z, h1 = R1.e - R1.z, h2 = R2.e - R2.z;
 
-    // -------- y switch of row r-1, y dissipation flux through the face between rows r-2 and r-1
+    // -------- y switch of row r-1, y dissipation flux through the face between
+    // rows r-2 and r-1 (north face of the corrector's row, south face of the predictor's)
+    V FYQ[3];
     if (KAPPA) {
         const bool face_in = !brow || (r - 2 >= 0 && r - 1 < ny);
         const V nyn = nu_switch(h2, h1, h0);
         V eps = face_eps(h2 > hdv, h1 > hdv, Cy.NY[O], nyn);
         if (!face_in) eps = V(T(0));
-        Cy.FY[Q][0] = dflux(eps, R1.e, R2.e);
-        Cy.FY[Q][1] = dflux(eps, R1.u, R2.u);
-        Cy.FY[Q][2] = dflux(eps, R1.v, R2.v);
+        FYQ[0] = dflux(eps, R1.e, R2.e);
+        FYQ[1] = dflux(eps, R1.u, R2.u);
+        FYQ[2] = dflux(eps, R1.v, R2.v);
         Cy.NY[Q] = nyn;
     }
 
@@ -377,21 +385,18 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         const Row<T, CPT>& c = R1;
         const Row<T, CPT>& yn = SY > 0 ? R0 : R2;
         const V hyn = SY > 0 ? h0 : h2;
-        // x neighbours: on the predictor's side with the ring halo (that edge lane outputs)
+        // x neighbours on the predictor's side: the lane's next cells, the outer one from the ring
         const int hcol = SX > 0 ? I.col + CPT : I.col - 1;
-        const bool edge_lane = SX > 0 ? lane == 31 : lane == 0;
         Row<T, CPT> xn;
-        xn.e = shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), edge_lane);
-        xn.u = shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), edge_lane);
-        xn.v = shift<SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, hcol), edge_lane);
-        xn.z = shift<SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, hcol), edge_lane);
-        if (brow && (r - 1 < 0 || r - 1 >= ny)) {  // halo column of a ghost row
+        xn.e = shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), true);
+        xn.u = shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), true);
+        xn.v = shift<SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, hcol), true);
+        xn.z = shift<SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, hcol), true);
+        if (brow && (r - 1 < 0 || r - 1 >= ny)) {  // the cell read from the ring in a ghost row
             constexpr int j = SX > 0 ? CPT - 1 : 0;
-            if (edge_lane) {
-                Cell<T> q; q.e = xn.e[j]; q.u = xn.u[j]; q.v = xn.v[j]; q.z = xn.z[j];
-                q = ghost(q, r - 1 < 0 ? SIDE_S : SIDE_N, G);
-                xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
-            }
+            Cell<T> q; q.e = xn.e[j]; q.u = xn.u[j]; q.v = xn.v[j]; q.z = xn.z[j];
+            q = ghost(q, r - 1 < 0 ? SIDE_S : SIDE_N, G);
+            xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
         }
         const V qx = h1 * c.u, qy = h1 * c.v;
         const V qxn = (xn.e - xn.z) * xn.u;
@@ -449,13 +454,14 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             ia.clamp = fma_(T(0.5), added, ia.clamp);
 
         if (KAPPA) {
-            // x dissipation of row r-1: the other side's neighbours need no halo
-            // (the lane at that strip edge never outputs)
+            // x dissipation of row r-1; the outer neighbour on the other side
+            // from the ring as well
             Row<T, CPT> xo;
-            xo.e = shift<-SX, T, CPT>(c.e, T(0), false);
-            xo.u = shift<-SX, T, CPT>(c.u, T(0), false);
-            xo.v = shift<-SX, T, CPT>(c.v, T(0), false);
-            xo.z = shift<-SX, T, CPT>(c.z, T(0), false);
+            const int ocol = SX > 0 ? I.col - 1 : I.col + CPT;
+            xo.e = shift<-SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, ocol), true);
+            xo.u = shift<-SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, ocol), true);
+            xo.v = shift<-SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, ocol), true);
+            xo.z = shift<-SX, T, CPT>(c.z, ld1<T, CPT>(s1, 3, ocol), true);
             const Row<T, CPT>& L = SX > 0 ? xo : xn;  // left neighbours
             const Row<T, CPT>& Rr = SX > 0 ? xn : xo; // right neighbours
             V hl = L.e - L.z, hr = Rr.e - Rr.z;
@@ -467,16 +473,21 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 }
             }
             const V nuc = nu_switch(hl, h1, hr);
-            // switch one column outside the lane: adjacent lane, or from the ring at the output edge
-            T nu_lo = shup(nuc[CPT - 1]), nu_hi = shdn(nuc[0]);
+            // switch one column outside the lane: on the predictor's side every lane
+            // computes it from the ring (at the grid edge with the ghost depth
+            // beyond it, as the adjacent lane would); on the other side the
+            // adjacent lane's (the edge lane there never outputs)
+            T nu_lo, nu_hi;
             if (SX > 0) {
-                const T h2x = ld1<T, CPT>(s1, 0, I.col + CPT + 1) - ld1<T, CPT>(s1, 3, I.col + CPT + 1);
-                const T ext = nu_switch(h1[CPT - 1], hr[CPT - 1], h2x);
-                nu_hi = lane == 31 ? ext : nu_hi;
+                T h2x = ld1<T, CPT>(s1, 0, I.col + CPT + 1) - ld1<T, CPT>(s1, 3, I.col + CPT + 1);
+                if (edge && I.x0c + CPT == nx - 1) h2x = hr[CPT - 1];
+                nu_hi = nu_switch(h1[CPT - 1], hr[CPT - 1], h2x);
+                nu_lo = shup(nuc[CPT - 1]);
             } else {
-                const T h2x = ld1<T, CPT>(s1, 0, I.col - 2) - ld1<T, CPT>(s1, 3, I.col - 2);
-                const T ext = nu_switch(h2x, hl[0], h1[0]);
-                nu_lo = lane == 0 ? ext : nu_lo;
+                T h2x = ld1<T, CPT>(s1, 0, I.col - 2) - ld1<T, CPT>(s1, 3, I.col - 2);
+                if (edge && I.x0c - 1 == 0) h2x = hl[0];
+                nu_lo = nu_switch(h2x, hl[0], h1[0]);
+                nu_hi = shdn(nuc[0]);
             }
             // east face of every cell
             V nur;
@@ -500,7 +511,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 west[0] = fl0[f];
 #pragma unroll
                 for (int j = 1; j < CPT; ++j) west[j] = fr[f][j - 1];
-                Cy.DX[Q][f] = fr[f] - west;
+                Cy.DX[Q][f] = (fr[f] - west) - FYQ[f];
             }
         }
     };
@@ -570,12 +581,11 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         V ou = half * (cs.u + uo);
         V ov = half * (cs.v + vo);
         if (KAPPA) {
-            // the x face fluxes come as their difference (east minus west); the
-            // y ones are this row's north face and the previous row's
+            // east minus west minus south face flux, plus the north one
             const V kap(G.kappa);
-            oe = fma_(kap, Cy.DX[O][0] + (Cy.FY[Q][0] - Cy.FY[O][0]), oe);
-            ou = fma_(kap, Cy.DX[O][1] + (Cy.FY[Q][1] - Cy.FY[O][1]), ou);
-            ov = fma_(kap, Cy.DX[O][2] + (Cy.FY[Q][2] - Cy.FY[O][2]), ov);
+            oe = fma_(kap, Cy.DX[O][0] + FYQ[0], oe);
+            ou = fma_(kap, Cy.DX[O][1] + FYQ[1], ou);
+            ov = fma_(kap, Cy.DX[O][2] + FYQ[2], ov);
         }
         V ad = wetdry_fix(oe, ou, ov, cs.z, hd);
         V spj = cfl_speed(oe, ou, ov, cs.z, G);
@@ -599,7 +609,14 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         ia.clamp += own ? added : T(0);
         ia.smax = (own && sp > ia.smax) ? sp : ia.smax;
         ia.bad = ia.bad || (own && bad);
-        if (st) {
+        if constexpr (sizeof(T) == 4 && CPT == 2) {  // predicated stores: no branch in the row
+            const size_t o = (size_t)C * G.pitch + I.x0c;
+            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n"
+                         " @p st.global.v2.f32 [%1], {%2, %3};\n @p st.global.v2.f32 [%4], {%5, %6};\n"
+                         " @p st.global.v2.f32 [%7], {%8, %9};\n}"
+                         ::"r"((unsigned)st), "l"(A.e1 + o), "f"(oe[0]), "f"(oe[1]), "l"(A.u1 + o), "f"(ou[0]), "f"(ou[1]),
+                           "l"(A.v1 + o), "f"(ov[0]), "f"(ov[1]) : "memory");
+        } else if (st) {
             const size_t o = (size_t)C * G.pitch + I.x0c;
             st_vec<T, CPT>(A.e1 + o, oe);
             st_vec<T, CPT>(A.u1 + o, ou);
@@ -649,33 +666,39 @@ __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, 
         if (k < I.nr) issue_row<T, CPT>(I, k, tme, tmu, tmv, tmz);
     Cy.NY[0] = Cy.NY[1] = Vec<T, CPT>(T(0));
 #pragma unroll
-    for (int f = 0; f < 3; ++f) Cy.FY[0][f] = Cy.FY[1][f] = Cy.DX[0][f] = Cy.DX[1][f] = Vec<T, CPT>(T(0));
+    for (int f = 0; f < 3; ++f) Cy.DX[0][f] = Cy.DX[1][f] = Vec<T, CPT>(T(0));
     ItemAcc<T> ia;
     ia.clamp = ia.bw = ia.be = ia.bs = ia.bn = ia.smax = T(0);
     ia.bad = false;
     int k = 0;
+    int kf = 0;  // after a failed wait: the last row whose loads may have been issued is kf + NPRE
     const int ny = A.G.ny;
 #pragma unroll 1
     for (; k + 1 < I.nr; k += 2) {
         const int r = I.y0 - 2 + k;
         if (!I.edge && k >= 4 && r - 2 > 0 && r + 1 < ny) {
+            // both rows' loads and waits first, so that the two rows schedule as
+            // one block; the slots refilled were last read in the previous pair
+            fence_async_smem();
+            if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
+            if (k + 1 + NPRE < I.nr) issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz);
+            if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) { timed_out = true; kf = k + 1; break; }
             row_step<T, CPT, SX, SY, KAPPA, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            if (timed_out) break;
             row_step<T, CPT, SX, SY, KAPPA, 1, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
         } else {
             row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            if (timed_out) break;
+            if (timed_out) { kf = k; break; }
             row_step<T, CPT, SX, SY, KAPPA, 1, true>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            if (timed_out) { kf = k + 1; break; }
         }
-        if (timed_out) break;
     }
     if (!timed_out && k < I.nr) {
         row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-        ++k;
+        kf = k;
     }
     if (timed_out) {
         // drain this item's loads still in flight (bounded) before the ring is reused or left
-        const int issued = I.nr < k + NPRE ? I.nr : k + NPRE;
+        const int issued = I.nr < kf + NPRE + 1 ? I.nr : kf + NPRE + 1;
         for (int q = k; q < issued; ++q) {
             const unsigned g = I.g0 + (unsigned)q;
             unsigned long long t0 = clock64();

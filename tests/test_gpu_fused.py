@@ -23,6 +23,10 @@ CASES = {
     "dambreak": (lambda: I.dam_break(260, 90, seed=3), 300),
     "ragged": (lambda: I.dam_break(37, 23, seed=11), 150),
     "tall": (lambda: I.dam_break(9, 140, seed=12), 100),
+    # widths 62 k + 1: the last column's dissipation switch sits one column
+    # beyond a strip of 62 output columns (wet up to the east boundary)
+    "river125": (lambda: I.river(125, 60, seed=7), 200),
+    "basin63_k": (lambda: I.basin_hump(63, 50, manning_n=0.03, kappa=0.25), 200),
 }
 
 
@@ -70,7 +74,7 @@ def test_fused_fp32_matches_oracle(oracle, name):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("name", ["dambreak", "river", "ragged", "tall"])
+@pytest.mark.parametrize("name", ["dambreak", "river", "ragged", "tall", "river125", "basin63_k"])
 def test_fused_independent_of_decomposition(name, precision):
     """Bitwise identical state for different rows-per-item, and equal to the
     plain kernel."""
