@@ -384,7 +384,7 @@ template <class R, class T>
 __device__ __forceinline__ R wetdry_fix(R& e, R& u, R& v, R z, T h_dry) {
     const R h = e - z;
     const auto neg = h < R(T(0));
-    const R added = sel(neg, z - e, R(T(0)));  // -h, exactly
+    const R added = tmax(-h, R(T(0)));  // z - e (= -h exactly) when h < 0, else +0
     e = sel(neg, z, e);
     const auto dry = h <= R(h_dry);            // includes h < 0 (h_dry > 0)
     u = sel(dry, R(T(0)), u);

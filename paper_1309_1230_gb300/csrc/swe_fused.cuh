@@ -215,6 +215,8 @@ struct ItemCtx {
     int lane, xw, xb, col, x0c, y0, y1, nr;
     int yoff;                    // tensor row of the scenario's row 0
     bool out_lane, edge;
+    bool st_lane;                // the lane outputs and its first cell is in the grid
+    int plo, phi;                // rows of the item whose predicted clamps this item tallies
     unsigned g0;
 };
 
@@ -450,7 +452,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         P.e = eo; P.u = uo; P.v = vo; P.z = c.z;
         P.qy = (eo - c.z) * vo;
         // a predicted clamp counts once per cell: in the item and lane that output it
-        if (I.out_lane && p >= I.y0 && p < I.y1 && I.x0c >= 0 && p >= G.own_lo && p < G.own_hi)
+        if (I.st_lane && p >= I.plo && p < I.phi)
             ia.clamp = fma_(T(0.5), added, ia.clamp);
 
         if (KAPPA) {
@@ -604,7 +606,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             sp = spj[j] > sp ? spj[j] : sp;
             bad = bad || !(dsum[j] == T(0));
         }
-        const bool st = I.out_lane && I.x0c >= 0 && I.x0c < nx;
+        const bool st = I.st_lane;
         const bool own = st && C >= G.own_lo && C < G.own_hi;  // halo rows of a strip: stored, not tallied
         ia.clamp += own ? added : T(0);
         ia.smax = (own && sp > ia.smax) ? sp : ia.smax;
@@ -660,6 +662,9 @@ template <class T, int CPT, int SX, int SY, bool KAPPA>
 __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
                                          Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
                                          const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out) {
+    I.st_lane = I.out_lane && I.x0c >= 0 && I.x0c < A.G.nx;
+    I.plo = max(I.y0, A.G.own_lo);
+    I.phi = min(I.y1, A.G.own_hi);
     fence_async_smem();  // the previous item's rows were read through the generic proxy
 #pragma unroll
     for (int k = 0; k < NPRE; ++k)
