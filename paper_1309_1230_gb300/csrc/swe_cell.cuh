@@ -14,8 +14,8 @@
 // The stage functions are generic in the value type R: a scalar T, or a
 // lane vector vecn<T, N> holding the N cells one lane of the fused kernel
 // owns in a row.  vecn<float, 2> adds, multiplies and multiply-adds both
-// cells with one packed instruction (add/sub/mul/fma.rn.ftz.f32x2, sm_100
-// and later); everything else acts per cell.  Per component a packed
+// cells with one packed instruction (mul/fma.rn.ftz.f32x2, sm_100 and later;
+// sums as a multiply-add with a unit factor); everything else acts per cell.  Per component a packed
 // operation rounds exactly like its scalar one (IEEE round to nearest, FP32
 // subnormals flushed), so a cell's result does not depend on the value type
 // it was computed in.
@@ -232,10 +232,29 @@ struct vecn<float, 2> {
             : "=f"(r.v.x), "=f"(r.v.y) : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));                 \
         return r;                                                                                         \
     }
-    SWE_PACKED(operator+, "add.rn.ftz.f32x2")
-    SWE_PACKED(operator-, "sub.rn.ftz.f32x2")
     SWE_PACKED(operator*, "mul.rn.ftz.f32x2")
 #undef SWE_PACKED
+    // Sums and differences as a multiply-add with a unit factor: a + b =
+    // fma(a, 1, b) and a - b = fma(b, -1, a) round exactly as the add (the
+    // product is exact, signed zeros included).  With a packed add.rn, ptxas
+    // was seen to contract a packed product feeding it into one FFMA2 in some
+    // builds (1-ulp differences from the scalar kernels), although add.rn
+    // forbids that; a sum that already is a multiply-add leaves nothing to
+    // contract into.
+    friend __device__ __forceinline__ vecn operator+(vecn a, vecn b) {
+        vecn r;
+        asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+            " mov.b64 rc, 0x3F8000003F800000;\n fma.rn.ftz.f32x2 rd, ra, rc, rb;\n mov.b64 {%0, %1}, rd;\n}"
+            : "=f"(r.v.x), "=f"(r.v.y) : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+        return r;
+    }
+    friend __device__ __forceinline__ vecn operator-(vecn a, vecn b) {
+        vecn r;
+        asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+            " mov.b64 rc, 0xBF800000BF800000;\n fma.rn.ftz.f32x2 rd, rb, rc, ra;\n mov.b64 {%0, %1}, rd;\n}"
+            : "=f"(r.v.x), "=f"(r.v.y) : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+        return r;
+    }
     friend __device__ __forceinline__ vecn operator/(vecn a, vecn b) { return vecn(a.v.x / b.v.x, a.v.y / b.v.y); }
     friend __device__ __forceinline__ vecn smul(vecn a, vecn b) { return vecn(a.v.x * b.v.x, a.v.y * b.v.y); }
     friend __device__ __forceinline__ vecn fma_(vecn a, vecn b, vecn d) {

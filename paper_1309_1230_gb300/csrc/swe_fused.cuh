@@ -319,8 +319,9 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 // predictor and x dissipation of row r-1, and the corrector, average,
 // dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.  The
 // arithmetic works on the lane's CPT cells at once (Vec); boundary cases
-// patch single cells.
-template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN>
+// patch single cells.  NF (lean rows): 1 when a per-cell Manning field is
+// set, so that a lean row has no branch on it.
+template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int NF>
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
@@ -347,6 +348,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     // the x boundary, where every boundary test below is false.
     const bool brow = GEN && ((r - 2 <= 0) || (r >= ny));
     const bool edge = GEN && I.edge;
+    const bool nfield = GEN ? A.n2 != nullptr : NF != 0;
     const unsigned g = I.g0 + (unsigned)k;
     const unsigned char* s0 = I.ring + ((g) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
     const unsigned char* s1 = I.ring + ((g - 1u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
@@ -430,7 +432,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             }
         }
         V gn2v;
-        if (A.n2 != nullptr) {
+        if (nfield) {
             const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
             const int pr = p < 0 ? 0 : (p >= ny ? ny - 1 : p);
             ld_vec<T, CPT>(A.n2 + (size_t)pr * G.pitch + xc, gn2v);
@@ -568,7 +570,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             }
         }
         V gn2v;
-        if (A.n2 != nullptr) {
+        if (nfield) {
             const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
             ld_vec<T, CPT>(A.n2 + (size_t)C * G.pitch + xc, gn2v);
         } else {
@@ -688,17 +690,22 @@ __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, 
             if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
             if (k + 1 + NPRE < I.nr) issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz);
             if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) { timed_out = true; kf = k + 1; break; }
-            row_step<T, CPT, SX, SY, KAPPA, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            row_step<T, CPT, SX, SY, KAPPA, 1, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            if (A.n2 != nullptr) {
+                row_step<T, CPT, SX, SY, KAPPA, 0, false, 1>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+                row_step<T, CPT, SX, SY, KAPPA, 1, false, 1>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            } else {
+                row_step<T, CPT, SX, SY, KAPPA, 0, false, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+                row_step<T, CPT, SX, SY, KAPPA, 1, false, 0>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            }
         } else {
-            row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            row_step<T, CPT, SX, SY, KAPPA, 0, true, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
             if (timed_out) { kf = k; break; }
-            row_step<T, CPT, SX, SY, KAPPA, 1, true>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            row_step<T, CPT, SX, SY, KAPPA, 1, true, 0>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
             if (timed_out) { kf = k + 1; break; }
         }
     }
     if (!timed_out && k < I.nr) {
-        row_step<T, CPT, SX, SY, KAPPA, 0, true>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+        row_step<T, CPT, SX, SY, KAPPA, 0, true, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
         kf = k;
     }
     if (timed_out) {
