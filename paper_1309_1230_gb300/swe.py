@@ -384,14 +384,6 @@ class Batch:
         self._chk(self.lib.swe_batch_step(self.b, int(nsteps), infos))
         return [_info(x) for x in infos] if want_info else None
 
-    def set_own_rows(self, lo: int, hi: int):
-        """Rows [lo, hi) are this strip's own; the rest are halo rows."""
-        _check(self.lib.swe_set_own_rows(self.ctx, int(lo), int(hi)), self.ctx)
-
-    def copy_rows_from(self, src: "Solver", src_row: int, dst_row: int, nrows: int):
-        """Copies nrows rows of src's current level into this context."""
-        _check(self.lib.swe_copy_rows(self.ctx, int(dst_row), src.ctx, int(src_row), int(nrows)), self.ctx)
-
     def autotune(self, probe_steps: int = 10, rows=None):
         """Times each candidate rows-per-item on the current states (which are
         restored) and keeps the fastest; returns (chosen, {rows: ms per step})."""
