@@ -46,11 +46,22 @@ FUSED_SOURCES = ["paper_1309_1230_gb300/csrc/swe_fused.cuh", "paper_1309_1230_gb
                  "paper_1309_1230_gb300/csrc/swe_fused.cu"]
 
 
+_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def _code_only(src: str) -> str:
+    """The source with comments removed and whitespace collapsed (string
+    literals kept), so that a comment edit does not change the hash."""
+    out = _TOKENS.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", src)
+    return " ".join(out.split())
+
+
 def sources_sha() -> str:
+    """Hash of the fused kernel's code (comments and whitespace ignored)."""
     h = hashlib.sha256()
     for p in FUSED_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

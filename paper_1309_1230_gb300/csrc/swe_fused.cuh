@@ -5,28 +5,30 @@
 // the host set-up (tensor maps, work plan) is in swe_fused.cu.
 #pragma once
 //
-// Decomposition.  A work item is a column strip of 32*CPT cells (one warp, CPT
-// cells per lane) by a segment of L rows; the resident warps take items from
-// a per-step atomic queue, costliest first, so that they finish together.  Along x the warp outputs 31 of its
-// 32 lanes: the remaining lane (lane 0 when the predictor differences
-// forward, lane 31 when backward) only computes the predicted values its
-// neighbour's corrector needs.  Along y the warp marches row by row; the
-// dependency radius of one step is one row for predictor and corrector and
-// two rows for the dissipation switch, so the warp loads the segment plus two
-// rows above and below.
+// Decomposition.  A work item is a column strip of 32*CPT cells (one warp,
+// CPT cells per lane) by a segment of L rows; the resident warps take items
+// from a per-step atomic queue, costliest first, so that they finish
+// together.  Along x the warp outputs 31 of its 32 lanes: the remaining lane
+// (lane 0 when the predictor differences forward, lane 31 when backward) only
+// computes the predicted values its neighbour's corrector needs.  Along y the
+// warp marches row by row; the dependency radius of one step is one row for
+// predictor and corrector and two rows for the dissipation switch, so the
+// warp loads the segment plus two rows above and below.
 //
 // Data movement.  Level-n rows (eta, u, v, z) stream into a per-warp ring in
 // shared memory with TMA (cp.async.bulk.tensor.2d, completion on an
 // mbarrier), NPRE rows ahead of use; a row stays in the ring while any of the
-// four rows of the step's stencil window still needs it.  The two predicted
-// rows and the y dissipation switches the corrector needs are carried in
+// four rows of the step's stencil window still needs it.  Interior rows are
+// loaded and waited for in pairs.  The two predicted rows, the y dissipation
+// switch and the partial dissipation sum the corrector needs are carried in
 // registers from one row to the next.  The level-n x neighbours outside a
 // lane's cells are read from the ring (its columns extend two cells beyond
 // the strip on both sides); the predicted ones come from adjacent lanes by
-// shuffles (the lane that would need a halo there never outputs).  Boundary handling runs under
-// warp-uniform branches: per row for the y sides, per item for the x sides.  The new level is stored with
-// 16-byte vector stores.  Out-of-grid rows and columns read as zeros (TMA
-// fill) and are replaced by the ghost cells of the boundary conditions.
+// shuffles (the lane that would need a halo there never outputs).  Boundary
+// handling runs under warp-uniform branches: per row for the y sides, per
+// item for the x sides.  The new level is stored with one vector store per
+// field and lane (both cells).  Out-of-grid rows and columns read as zeros
+// (TMA fill) and are replaced by the ghost cells of the boundary conditions.
 //
 // Reductions.  The CFL speed of the new level (the next step's S2) is reduced
 // per warp, per CTA, then with one atomicMax per CTA on the FP64 bit

@@ -85,3 +85,16 @@ def test_ctypes_layout_matches_the_header(tmp_path):
     want = [ctypes.sizeof(swe.swe_params), ctypes.sizeof(swe.swe_step_info),
             swe.swe_params.stream.offset, swe.swe_params.reserved.offset, swe.swe_step_info.flags.offset]
     assert got == want
+
+
+def test_kernel_hash_ignores_comments_only():
+    """bench.py reports the recorded DRAM traffic only while the kernel code
+    hashes to the captured value; comments and layout must not count, code
+    and string literals (inline PTX) must."""
+    import bench
+    a = 'int f(){ asm("mov.b64 %0, 1; // not a comment"); return 1; } // note\n/* block\ncomment */'
+    b = 'int f(){   asm("mov.b64 %0, 1; // not a comment");\n return 1; }'
+    c = 'int f(){ asm("mov.b64 %0, 2; // not a comment"); return 1; }'
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+    assert "not a comment" in bench._code_only(a)
