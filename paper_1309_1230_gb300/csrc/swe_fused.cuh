@@ -250,8 +250,9 @@ template <class T>
 __device__ __forceinline__ T shup(T x) { return __shfl_up_sync(FULL, x, 1); }
 
 // Values one column to the right (D > 0) or left (D < 0) of the lane's
-// cells: the lane's next cell, else the adjacent lane's end cell; the
-// strip-edge lane on that side takes `halo` when `use_halo`.
+// cells: the lane's next cell; for the outer one, `halo` when `use_halo`
+// (the caller read it from the ring), else the adjacent lane's end cell by
+// a shuffle.
 template <int D, class T, int CPT>
 __device__ __forceinline__ Vec<T, CPT> shift(const Vec<T, CPT>& a, T halo, bool use_halo) {
     Vec<T, CPT> o;
