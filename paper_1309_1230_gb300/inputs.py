@@ -183,3 +183,21 @@ def large_river(nx: int, ny: int, seed: int = 1314, chunk_rows: int = 2048) -> d
         u[j0:j1] = 0.1 * np.sin(2 * np.pi * y / 700.0 + ph[5]) + 0.0 * x
     return dict(nx=nx, ny=ny, dx=1.0, dy=1.0, z=z, eta=eta, u=u, v=v, manning_n=0.03, kappa=0.25,
                 bc=(INFLOW, OUTFLOW, WALL, WALL), q_in=(2.0, 0.0, 0.0, 0.0))
+
+
+def with_cell_size(case: dict, dx: float, dy: float) -> dict:
+    """The same arrays and settings on cells of dx by dy metres (the arrays
+    are given per cell, so only the two sizes change)."""
+    out = dict(case)
+    out["dx"], out["dy"] = float(dx), float(dy)
+    return out
+
+
+def open_river(nx: int, ny: int, seed: int = 1315, q_w: float = 2.0, q_s: float = 1.0) -> dict:
+    """River reach open on all four sides: inflow q_w through the west side
+    and q_s through the south side, free outflow east and north (every side
+    carries water), otherwise as `river`."""
+    c = river(nx, ny, seed=seed)
+    c["bc"] = (INFLOW, OUTFLOW, INFLOW, OUTFLOW)
+    c["q_in"] = (q_w, 0.0, q_s, 0.0)
+    return c

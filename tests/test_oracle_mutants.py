@@ -40,12 +40,24 @@ MUTANTS = {
     "dt cap ignored": ("return dt < p->dt_max ? dt : p->dt_max;", "return dt;"),
     "clamp tally weight": ("acc[0] += 0.5 * clamp_pred + clamp_final;", "acc[0] += clamp_pred + clamp_final;"),
     "east boundary tally sign": ("acc[2] -= dt * p->dy * be;", "acc[2] += dt * p->dy * be;"),
+    # face lengths of the side tallies and the cell area of the volume: only
+    # cells with dx != dy (and != 1) tell these apart
+    "west tally weighted by dx": ("acc[1] += dt * p->dy * bw;", "acc[1] += dt * p->dx * bw;"),
+    "east tally weighted by dx": ("acc[2] -= dt * p->dy * be;", "acc[2] -= dt * p->dx * be;"),
+    "south tally weighted by dy": ("acc[3] += dt * p->dx * bs;", "acc[3] += dt * p->dy * bs;"),
+    "north tally weighted by dy": ("acc[4] -= dt * p->dx * bn;", "acc[4] -= dt * p->dy * bn;"),
+    "volume without cell area": ("return s * p->dx * p->dy;", "return s;"),
+    "volume times dx only": ("return s * p->dx * p->dy;", "return s * p->dx;"),
+    "clamp tally without cell area": ("const double cell_area = p->dx * p->dy;", "const double cell_area = 1.0;"),
 }
 
 PIN_CALLS = [
     (pins.test_mass_conservation_closed_basin, dict(kappa=0.25)),
     (pins.test_volume_budget_open_boundaries, {}),
     (pins.test_volume_budget_with_drying, {}),
+    (pins.test_flat_lake_volume_closed_form, {}),
+    (pins.test_volume_budget_anisotropic_cells_all_sides_open, {}),
+    (pins.test_volume_budget_anisotropic_cells_with_drying, {}),
     (pins.test_lake_at_rest, dict(islands=True, kappa=0.25)),
     (pins.test_lake_at_rest, dict(islands=False, kappa=0.0)),
     (pins.test_reduces_to_separate_1d_code, dict(case="dambreak")),

@@ -75,6 +75,54 @@ def test_volume_budget_with_drying(oracle):
     assert np.min(r.eta - c["z"]) >= 0.0
 
 
+# Cells of 0.7 m by 1.9 m: a west/east face is dy long, a south/north face dx
+# long, and a cell holds h dx dy of water.  With dx = dy = 1 a swapped weight
+# would not show.
+DX_A, DY_A = 0.7, 1.9
+
+
+def test_flat_lake_volume_closed_form(oracle):
+    """A flat lake of depth H over a flat bed holds H times the domain area
+    nx dx by ny dy."""
+    nx, ny, H = 23, 17, 1.25
+    z = np.full((ny, nx), -0.5)
+    p = oracle.Params(nx=nx, ny=ny, dx=DX_A, dy=DY_A)
+    V = oracle.volume(p, z, z + H)
+    assert abs(V - H * (nx * DX_A) * (ny * DY_A)) <= 1e-13 * V
+
+
+def test_volume_budget_anisotropic_cells_all_sides_open(oracle):
+    """Inflow through the west and south sides, outflow east and north, on
+    0.7 m by 1.9 m cells: the volume change equals the sum of the four
+    tallied side inflows (each weighted by its own face length) plus the
+    clamp tally, and every side carries water."""
+    c = I.with_cell_size(I.open_river(96, 80, seed=17), DX_A, DY_A)
+    p = params_of(oracle, c)
+    r = oracle.run(p, c["z"], c["eta"], c["u"], c["v"], 250, nthreads=4)
+    assert r.status == 0
+    V0 = oracle.volume(p, c["z"], c["eta"])
+    V1 = oracle.volume(p, c["z"], r.eta)
+    assert r.bflux[0] > 0.0 and r.bflux[2] > 0.0
+    # none of the four terms is negligible next to the tolerance (the open
+    # sides let water out or, where the surface tilts back, in)
+    assert np.min(np.abs(r.bflux)) > 1e-3 * V0
+    budget = r.bflux.sum() + r.clamp_volume
+    assert abs((V1 - V0) - budget) <= 1e-11 * V0
+
+
+def test_volume_budget_anisotropic_cells_with_drying(oracle):
+    """Dam break onto dry ground on 0.7 m by 1.9 m cells: the volume changes
+    only by the clamp tally, which counts the added depth times dx dy."""
+    c = I.with_cell_size(I.dam_break(96, 64, seed=3), DX_A, DY_A)
+    p = params_of(oracle, c)
+    r = oracle.run(p, c["z"], c["eta"], c["u"], c["v"], 300)
+    assert r.status == 0
+    V0 = oracle.volume(p, c["z"], c["eta"])
+    V1 = oracle.volume(p, c["z"], r.eta)
+    assert r.clamp_volume > 1e-9 * V0
+    assert abs((V1 - V0) - r.clamp_volume) <= 1e-12 * V0
+
+
 # ---------------------------------------------------------------- lake at rest
 def _lake(nx, ny, seed, level, islands):
     rng = np.random.Generator(np.random.PCG64(seed))
