@@ -135,32 +135,53 @@ typedef struct swe_ctx swe_ctx;
  * directions, device 0, own stream); nx, ny, dx, dy still need setting. */
 void swe_params_default(swe_params* p);
 
-/* Validates p, allocates the context and its device buffers (state ping-pong,
- * bed, friction field, reduction scratch).  *out receives the context, or NULL
- * on failure.  Bed and state start at zero until set. */
+/* The grid and scheme settings of one problem (paper Sec. 1: a structured
+ * grid carrying eta, u, v; Sec. 3.1: the variable step's Courant number).
+ * Validates p (SWE_ERR_ARG on a bad size, cell size, constant, boundary code
+ * or kernel; SWE_ERR_CUDA when the device or an allocation fails) and
+ * allocates the context and its device buffers (state ping-pong, bed,
+ * friction field, reduction scratch); the context owns them.  *out receives
+ * the context, or NULL on failure.  Bed and state start at zero until set. */
 swe_status swe_create(const swe_params* p, swe_ctx** out);
 
-/* Bed elevation z (m) and, optionally, a per-cell Manning n field (NULL: the
- * uniform manning_n).  Host arrays, ny*nx. */
+/* The domain's topography (paper Sec. 4: each workload gives the domain
+ * topology and initial conditions): bed elevation z (m) and, optionally, a
+ * per-cell Manning n field (NULL: the uniform manning_n) for the friction
+ * sub-steps S6/S12.  Host arrays, ny*nx doubles, row-major, copied; the
+ * caller keeps ownership.  SWE_ERR_ARG for a NULL z or a non-finite or
+ * negative n; SWE_ERR_STATE on a poisoned context. */
 swe_status swe_set_bed(swe_ctx* ctx, const double* z, const double* n_field);
 
-/* Initial state (host arrays).  A depth below -1e-12 m is SWE_ERR_NEGDEPTH;
- * a smaller negative depth is clamped (eta = z); dry cells get zero velocity.
- * Computes the first step's CFL reduction.  Keeps the step index and time. */
+/* Initial conditions (paper Sec. 4) of the unknowns eta, u, v (Sec. 1): host
+ * arrays, ny*nx doubles, row-major, copied.  A depth below -1e-12 m is
+ * SWE_ERR_NEGDEPTH and a non-finite value SWE_ERR_ARG; after either the
+ * context holds no valid state (swe_step returns SWE_ERR_STATE until a state
+ * is set again).  A smaller negative depth is
+ * clamped (eta = z); dry cells get zero velocity (the drying rule read from
+ * Sec. 6.2).  Computes the first step's
+ * CFL reduction (S2, Sec. 3.1).  Keeps the step index and time. */
 swe_status swe_set_state(swe_ctx* ctx, const double* eta, const double* u, const double* v);
 
 /* Sets the step index (direction parity) and the simulated time. */
 swe_status swe_set_clock(swe_ctx* ctx, int64_t step, double t);
 
-/* Advances nsteps steps.  dt_fixed (nullable, host, nsteps values) replaces
- * S2 by the given step sizes; dt_out (nullable, host, nsteps values) receives
- * the step sizes used; info (nullable) receives the diagnostics at the end of
- * the call (reading it synchronises the stream).  SWE_ERR_NONFINITE when the
- * state holds NaN/Inf at the end. */
+/* Advances nsteps explicit MacCormack steps, each the 16 sub-steps of paper
+ * Sec. 1 with the variable step size of Sec. 3.1 (computed on the GPU, not
+ * copied to the host as the paper's code did).  dt_fixed (nullable, host,
+ * nsteps values) replaces S2 by the given step sizes; dt_out (nullable, host,
+ * nsteps values) receives the step sizes used; info (nullable) receives the
+ * diagnostics at the end of the call (reading it synchronises the stream).
+ * SWE_ERR_STATE before a state is set or on a poisoned context;
+ * SWE_ERR_NONFINITE when the state holds NaN/Inf at the end (Sec. 4 reports
+ * NaNs in one Fortran run); SWE_ERR_TIMEOUT when a bounded device wait gave
+ * up.  After either the context still accepts calls: the step index has
+ * advanced, the state is what the steps left (set a new one to go on). */
 swe_status swe_step(swe_ctx* ctx, int32_t nsteps, const double* dt_fixed, double* dt_out,
                     swe_step_info* info);
 
-/* Current state to host arrays (synchronises the stream). */
+/* The unknowns of the current level (paper Sec. 1: elevation and the two
+ * velocities per cell) to host arrays, ny*nx doubles each, caller-owned
+ * (synchronises the stream).  SWE_ERR_ARG for a NULL array. */
 swe_status swe_get_state(swe_ctx* ctx, double* eta, double* u, double* v);
 
 /* Diagnostics of the current state (synchronises the stream). */
@@ -175,7 +196,8 @@ swe_status swe_set_bed_device(swe_ctx* ctx, const void* z, const void* n_field);
 /* The context's CUDA stream (cudaStream_t). */
 void* swe_stream(const swe_ctx* ctx);
 
-/* Frees the context and every buffer it owns.  NULL is ignored. */
+/* Frees the context and every buffer it owns (the paper has no counterpart;
+ * it ends the problem created by swe_create).  NULL is ignored. */
 void swe_destroy(swe_ctx* ctx);
 
 /* Discrete adjoint (reverse mode) of nsteps steps from the current state: the
@@ -268,26 +290,31 @@ swe_status swe_batch_autotune(swe_batch* b, int32_t probe_steps, const int32_t* 
 void swe_batch_destroy(swe_batch* b);
 const char* swe_batch_last_error(const swe_batch* b);
 
-/* No-allocation FP32 step.  The paper has no counterpart to this entry point:
- * it serves callers that cannot allocate device memory -- code that runs while
- * a stream is being captured into a CUDA graph, engines whose device memory
- * is all handed out by their own pool, loops that cannot wait on the
- * allocator.  The caller passes device arrays (float, dense ny*nx, row-major)
- * of the bed and the input state, and separate output arrays (no aliasing);
- * the call queues one plain step (predictor and corrector kernels, the
- * scheme of the header comment, uniform Manning n) on `stream` (NULL: the
- * default stream) of the current device and allocates nothing.  Its scratch
- * -- the predicted planes, the reduction control block and the step size --
- * is one static device array of SWE_NOALLOC_MAX_CELLS cells (12 MB) that
- * every GPU loading this library holds until the process exits; grids above
- * that size are rejected with SWE_ERR_ARG.  dt_fixed > 0 gives the step size,
- * 0 computes it from the CFL rule; dt_out (host, nullable) receives the step
- * size used and then the call waits for the stream.  The predictor direction
- * is that of step 0 of dir_cycle.  The first call on a device looks up the
- * scratch's device address (once per device); make that first call before
- * any stream capture.  Every call shares the one array and the previous
- * call's contents are cleared or overwritten: calls that overlap on the GPU
- * (other streams, other threads) race. */
+/* No-allocation FP32 step.  The paper has no counterpart to this entry point.
+ * It serves callers that cannot allocate device memory: engines whose device
+ * memory is all handed out by their own pool (a cudaMalloc behind the pool's
+ * back breaks its budget), plug-ins running inside a host application that
+ * owns the device memory, and loops with hard latency limits that cannot wait
+ * on the allocator (cudaMalloc and cudaFree may synchronise the device).  The
+ * caller passes device arrays (float, dense ny*nx, row-major) of the bed and
+ * the input state, and separate output arrays: an output sharing any byte
+ * with an input or another output is SWE_ERR_ARG.  The call queues one plain
+ * step (predictor and corrector kernels, the scheme of the header comment,
+ * uniform Manning n) on `stream` (NULL: the default stream) of the current
+ * device and allocates nothing.  Its scratch -- the predicted planes, the
+ * reduction control block and the step size -- is one static device array of
+ * SWE_NOALLOC_MAX_CELLS cells (12 MB) that every GPU loading this library
+ * holds until the process exits; grids above that size are rejected with
+ * SWE_ERR_ARG.  dt_fixed > 0 gives the step size (passed to the GPU by
+ * value), 0 computes it from the CFL rule.  dt_out (host, nullable) receives
+ * the step size used; with it the call waits for the stream and returns
+ * SWE_ERR_NONFINITE if the new state holds NaN or Inf.  Without dt_out the
+ * call does not wait and does not check for non-finite values.  The predictor
+ * direction is that of step 0 of dir_cycle.  The first call on a device looks
+ * up the scratch's device address (once per device, kept until the process
+ * exits; do not call this entry point on a device after cudaDeviceReset).
+ * Every call shares the one array, whose control block each call clears
+ * first: calls that overlap on the GPU (other streams, other threads) race. */
 #define SWE_NOALLOC_MAX_CELLS (1 << 20)
 swe_status swe_step_plain_f32_noalloc(const swe_params* p, const float* z, const float* eta, const float* u,
                                       const float* v, float* eta_out, float* u_out, float* v_out, double dt_fixed,

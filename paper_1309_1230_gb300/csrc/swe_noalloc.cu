@@ -1,9 +1,10 @@
 // swe_noalloc.cu -- the no-allocation FP32 step (swe_step_plain_f32_noalloc).
 //
-// For callers that must not allocate device memory: code running while a
-// CUDA stream is being captured into a graph (an allocation there breaks the
-// capture), engines whose device memory is all handed out by their own pool,
-// and loops with hard latency limits that cannot wait on the allocator.
+// For callers that must not allocate device memory: engines whose device
+// memory is all handed out by their own pool (a cudaMalloc behind the pool's
+// back breaks its budget), plug-ins running inside a host application that
+// owns the device memory, and loops with hard latency limits that cannot wait
+// on the allocator (cudaMalloc and cudaFree may synchronise the device).
 // Such a caller owns the state buffers; the step's own scratch (the predicted
 // planes, the reduction control block and the step size) lives in one
 // file-scope __device__ array that every GPU loading this library keeps until
@@ -22,7 +23,7 @@ namespace {
 
 struct NoallocScratch {
     swe::DevCtl ctl;          // CFL reduction slots and step bookkeeping; cleared by every call
-    double dt_in;             // a caller's fixed step size, copied in
+    double dt_in;             // a caller's fixed step size (k_noalloc_set_dt)
     double dt_used[2];        // the step size the call used
     float planes[3][SWE_NOALLOC_MAX_CELLS];  // predicted eta, u, v
 };
@@ -35,7 +36,10 @@ std::mutex g_mu;
 NoallocScratch* g_dev_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device (host code may not use
-// the symbol itself: it names a host-side stand-in).
+// the symbol itself: it names a host-side stand-in).  Looked up once per
+// device and kept for the life of the process; after a cudaDeviceReset the
+// module is loaded anew and the kept address is stale, so the entry point
+// must not be called on a device that was reset.
 cudaError_t scratch_on(int device, NoallocScratch** out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -48,6 +52,16 @@ cudaError_t scratch_on(int device, NoallocScratch** out) {
     }
     *out = g_dev_ptr[device];
     return cudaSuccess;
+}
+
+// Stores a caller's fixed step size, passed by value, where the step kernels
+// read it.
+__global__ void k_noalloc_set_dt(double* dst, double dt) { *dst = dt; }
+
+// Whether the byte ranges [a, a + n) and [b, b + n) share a byte.
+bool overlap(const void* a, const void* b, size_t n) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
 }
 
 }  // namespace
@@ -65,12 +79,17 @@ extern "C" swe_status swe_step_plain_f32_noalloc(const swe_params* p, const floa
     for (int s = 0; s < 4; ++s)
         if (p->bc[s] < SWE_BC_WALL || p->bc[s] > SWE_BC_OUTFLOW) return SWE_ERR_ARG;
     if (!(dt_fixed >= 0)) return SWE_ERR_ARG;
-    // the corrector reads the input level while writing the output level
-    const float* ins[3] = {eta, u, v};
-    const float* outs[3] = {eta_out, u_out, v_out};
-    for (const float* a : ins)
-        for (const float* b : outs)
-            if (a == b) return SWE_ERR_ARG;
+    // The corrector reads the input level (and the bed) while it writes the
+    // output level: no output may share a byte with an input or another output.
+    const size_t bytes = (size_t)p->nx * (size_t)p->ny * sizeof(float);
+    const void* ins[4] = {z, eta, u, v};
+    const void* outs[3] = {eta_out, u_out, v_out};
+    for (int i = 0; i < 3; ++i) {
+        for (const void* a : ins)
+            if (overlap(a, outs[i], bytes)) return SWE_ERR_ARG;
+        for (int j = i + 1; j < 3; ++j)
+            if (overlap(outs[i], outs[j], bytes)) return SWE_ERR_ARG;
+    }
 
     cudaStream_t st = (cudaStream_t)stream;
     int dev = -1;
@@ -82,17 +101,21 @@ extern "C" swe_status swe_step_plain_f32_noalloc(const swe_params* p, const floa
     if (cudaMemsetAsync(&s->ctl, 0, sizeof(s->ctl), st) != cudaSuccess) return SWE_ERR_CUDA;
     const double* dtp = nullptr;
     if (dt_fixed > 0) {
-        if (cudaMemcpyAsync(&s->dt_in, &dt_fixed, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return SWE_ERR_CUDA;
+        k_noalloc_set_dt<<<1, 1, 0, st>>>(&s->dt_in, dt_fixed);
+        if (cudaGetLastError() != cudaSuccess) return SWE_ERR_CUDA;
         dtp = &s->dt_in;
     }
     cudaError_t e = swe_plain_step_f32_raw(p, p->nx, z, eta, u, v, eta_out, u_out, v_out, s->planes[0],
                                            s->planes[1], s->planes[2], &s->ctl, dtp, s->dt_used, st);
     if (e != cudaSuccess) return SWE_ERR_CUDA;
     if (dt_out) {
+        unsigned flags = 0u;
         if (cudaMemcpyAsync(dt_out, &s->dt_used[0], sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return SWE_ERR_CUDA;
+        if (cudaMemcpyAsync(&flags, &s->ctl.flags, sizeof(flags), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return SWE_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return SWE_ERR_CUDA;
+        if (flags & SWE_FLAG_NONFINITE) return SWE_ERR_NONFINITE;
     }
     return SWE_OK;
 }
