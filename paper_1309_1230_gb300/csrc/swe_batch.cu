@@ -64,6 +64,8 @@ struct BatchArgs {
     long long step0;
     int nsteps, nitems, nscen, L, cur0, dir_cycle, dry_skip;
     int inflow_side[4];
+    unsigned long long bar_limit;  // grid-barrier wait limit, cycles
+    int withhold;          // test hook: CTA withhold - 1 skips its first barrier arrival (0: none)
 };
 
 constexpr unsigned long long BARRIER_LIMIT = 4000000000ull;  // cycles (~2 s)
@@ -79,9 +81,12 @@ __device__ __forceinline__ unsigned ld_acquire32(const unsigned* p) {
     return v;
 }
 
-// Bounded grid barrier (one warp per CTA); false when the wait gave up.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+// Bounded grid barrier (one warp per CTA); false when the wait gave up.  A
+// CTA told to withhold its arrival (a test hook) returns false at once, and
+// the other CTAs' waits run out after `limit` cycles.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned long long limit, bool withhold) {
     __syncwarp();
+    if (withhold) return false;
     unsigned ok = 1;
     if (threadIdx.x == 0) {
         const unsigned gen = ld_acquire32(bar + 1);
@@ -94,7 +99,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
         } else {
             const unsigned long long t0 = clock64();
             while (ld_acquire32(bar + 1) == gen) {
-                if (clock64() - t0 > BARRIER_LIMIT) { ok = 0; break; }
+                if (clock64() - t0 > limit) { ok = 0; break; }
                 __nanosleep(100);
             }
         }
@@ -239,7 +244,8 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
             }
             if (timed_out) break;
         }
-        if (timed_out || !grid_barrier(B.bar, gridDim.x)) {
+        const bool hold = B.withhold > 0 && blockIdx.x == (unsigned)(B.withhold - 1) && st == 0;
+        if (timed_out || !grid_barrier(B.bar, gridDim.x, B.bar_limit, hold)) {
             timed_out = true;
             if (lane == 0) atomicOr(&B.ctl[0].flags, (unsigned)SWE_FLAG_TIMEOUT);
         }
@@ -362,6 +368,8 @@ struct swe_batch {
     double* vol = nullptr;
     long long* wet = nullptr;
     int nitems = 0, grid = 0, L = 64;
+    unsigned long long bar_limit = BARRIER_LIMIT;  // cycles; params reserved[0] (test hook)
+    int withhold = 0;      // params reserved[1] (test hook), cleared after the next launch
     CUtensorMap tm[2][3];
     CUtensorMap tmz;
     cudaStream_t stream = nullptr;
@@ -438,6 +446,8 @@ BatchArgs make_args(const swe_batch* b, int nsteps) {
     B.step0 = b->step;
     B.nsteps = nsteps; B.nitems = b->nitems; B.nscen = b->count; B.L = b->L; B.cur0 = b->cur;
     B.dir_cycle = p.dir_cycle; B.dry_skip = p.dry_skip;
+    B.bar_limit = b->bar_limit;
+    B.withhold = b->withhold;
     return B;
 }
 
@@ -547,9 +557,14 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
         if (p->bc[s] < SWE_BC_WALL || p->bc[s] > SWE_BC_OUTFLOW || !std::isfinite(p->q_in[s])) return SWE_ERR_ARG;
     for (int s = 0; s < count; ++s)
         if (nx[s] < 1 || ny[s] < 1 || !(manning_n[s] >= 0)) return SWE_ERR_ARG;
+    // test hooks: the barrier wait limit (microseconds, at most 10 s) and a CTA withholding its arrival
+    if (p->reserved[0] < 0 || p->reserved[0] > 10000000 || p->reserved[1] < 0) return SWE_ERR_ARG;
     swe_batch* b = new (std::nothrow) swe_batch();
     if (!b) return SWE_ERR_ARG;
     b->p = *p;
+    // clock64 counts SM cycles: 2000 per microsecond at the GB300's 2.07 GHz maximum clock
+    if (p->reserved[0] > 0) b->bar_limit = (unsigned long long)p->reserved[0] * 2000ull;
+    b->withhold = p->reserved[1];
     b->count = count;
     b->nx.assign(nx, nx + count);
     b->ny.assign(ny, ny + count);
@@ -689,7 +704,7 @@ static cudaError_t launch_steps(swe_batch* b, int nsteps, bool graph) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->counters, 0, 3 * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
-    if (!graph) return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream);
+    if (!graph || b->withhold) return cudaLaunchCooperativeKernel(kern, dim3(b->grid), dim3(32), args, Gm::WARP_SMEM, b->stream);
     if (!b->graph || b->graph_steps != nsteps || b->graph_k != b->step || b->graph_cur != b->cur) {
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
         cudaGraph_t g = nullptr;
@@ -731,7 +746,10 @@ swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos) {
     }
     k_batch_begin<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
     BCK(b, cudaGetLastError());
-    if (nsteps > 0) BCK(b, launch_steps(b, nsteps, b->p.use_graph != 0));
+    if (nsteps > 0) {
+        BCK(b, launch_steps(b, nsteps, b->p.use_graph != 0));
+        b->withhold = 0;  // the test hook acts on one call
+    }
     b->step += nsteps;
     b->cur = (b->cur + nsteps) & 1;
     BCK(b, cudaMemcpyAsync(b->h_ctl, b->ctl, b->count * sizeof(DevCtl), cudaMemcpyDeviceToHost, b->stream));

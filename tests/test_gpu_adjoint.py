@@ -24,7 +24,8 @@ def _case(nx=32, ny=28, seed=4, bc=(0, 0, 0, 0), q_in=(0.0,) * 4):
 
 def _solver(c, nfield, precision):
     from paper_1309_1230_gb300 import swe
-    s = swe.Solver(c["nx"], c["ny"], manning_n=0.03, kappa=0.0, bc=c["bc"], q_in=c["q_in"], precision=precision)
+    s = swe.Solver(c["nx"], c["ny"], dx=c["dx"], dy=c["dy"], manning_n=0.03, kappa=0.0, bc=c["bc"], q_in=c["q_in"],
+                   precision=precision)
     s.set_bed(c["z"], nfield)
     s.set_state(c["eta"], c["u"], c["v"])
     return s
@@ -39,23 +40,63 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("bcs", ["walls", "open"])
+@pytest.mark.parametrize("bcs", ["walls", "open", "open_aniso"])
 def test_gpu_adjoint_matches_oracle_adjoint(oracle, bcs):
+    """32 x 28 cells, 40 steps; "open_aniso" on cells of 0.7 m by 1.9 m."""
     from paper_1309_1230_gb300 import swe
     bc, q = ((0, 0, 0, 0), (0.0,) * 4) if bcs == "walls" else ((1, 2, 0, 2), (0.4, 0.0, 0.0, 0.0))
     c, nfield = _case(bc=bc, q_in=q)
+    if bcs == "open_aniso":
+        c = I.with_cell_size(c, 0.7, 1.9)
     T = 40
     obs = _obs(c, T)
     s = _solver(c, nfield, swe.SWE_FP64)
     loss, gn, ge = s.adjoint(T, c["gauges"], obs)
     s.close()
-    p = oracle.Params(nx=c["nx"], ny=c["ny"], manning_n=0.03, kappa=0.0, bc=bc, q_in=q)
+    p = oracle.Params(nx=c["nx"], ny=c["ny"], dx=c["dx"], dy=c["dy"], manning_n=0.03, kappa=0.0, bc=bc, q_in=q)
     fwd = oracle.run(p, c["z"], c["eta"], c["u"], c["v"], T, nfield=nfield)
     ref = oracle.adjoint(p, c["z"], nfield, c["eta"], c["u"], c["v"], fwd.dt, c["gauges"], obs)
     assert ref.status == 0
     assert loss == pytest.approx(ref.loss, rel=1e-10)
     assert _rel(gn, ref.grad_n) <= 1e-10
     assert _rel(ge, ref.grad_eta0) <= 1e-10
+
+
+def test_gpu_adjoint_on_the_512_grid_matches_oracle_adjoint(oracle):
+    """The adjoint workload's own grid: 512 x 512 cells, Gaussian-sum bed,
+    fully wet, kappa 0, gradient at the uniform n = 0.03, over 120 steps (the
+    oracle keeps every forward state, 0.95 GB at this size) with the default
+    sqrt(T) checkpoints (11).  In 120 steps the hump's wave travels about 30
+    cells, so 8 gauges within 24 cells of the centre join the 16 uniform ones
+    (otherwise no gauge sees moving water and the Manning gradient is zero).
+    FP64 against the oracle's adjoint at 1e-10; FP32 against FP64 within
+    1e-3 of each gradient's scale."""
+    from paper_1309_1230_gb300 import swe
+    c = I.adjoint_case(512, 512)
+    T = 120
+    rng = np.random.Generator(np.random.PCG64(512))
+    gi, gj = rng.integers(256 - 24, 256 + 24, 8), rng.integers(256 - 24, 256 + 24, 8)
+    c["gauges"] = np.concatenate([c["gauges"], gj * 512 + gi]).astype(np.int64)
+    nfield = np.full((512, 512), 0.03)
+    obs = _obs(c, T, seed=21)
+    res = {}
+    for prec in (swe.SWE_FP64, swe.SWE_FP32):
+        s = _solver(c, nfield, prec)
+        res[prec] = s.adjoint(T, c["gauges"], obs)
+        s.close()
+    loss, gn, ge = res[swe.SWE_FP64]
+    p = oracle.Params(nx=512, ny=512, manning_n=0.03, kappa=0.0)
+    fwd = oracle.run(p, c["z"], c["eta"], c["u"], c["v"], T, nfield=nfield, nthreads=8)
+    ref = oracle.adjoint(p, c["z"], nfield, c["eta"], c["u"], c["v"], fwd.dt, c["gauges"], obs)
+    assert ref.status == 0
+    assert loss == pytest.approx(ref.loss, rel=1e-10)
+    assert _rel(gn, ref.grad_n) <= 1e-10
+    assert _rel(ge, ref.grad_eta0) <= 1e-10
+    for g in (gn, ge):  # neither gradient is trivial: both spread over thousands of cells
+        assert np.count_nonzero(np.abs(g) > 1e-6 * np.max(np.abs(g))) > 1000
+    l32, gn32, ge32 = res[swe.SWE_FP32]
+    assert l32 == pytest.approx(loss, rel=1e-4)
+    assert _rel(gn32, gn) <= 1e-3 and _rel(ge32, ge) <= 1e-3, (_rel(gn32, gn), _rel(ge32, ge))
 
 
 def test_gpu_adjoint_matches_central_differences():

@@ -11,7 +11,12 @@ times (fused kernel, automatic work plan).
   cells after 1000 steps, the same with IEEE-accurate division, square root
   and pow).  The bounds below are the relative L2 error (measured 2e-6 to
   4e-6), the share of cells beyond 1e-4 (measured < 0.02 %) and the max.
-* River 8192^2 (the benchmark grid): the FP32 GPU step against the oracle on
+* River 8192^2 (the benchmark grid), its full 500 steps: the FP32 GPU step
+  against the FP64 GPU step (the fused sweep in FP64, which the tests above
+  and the other parity files hold to 1e-10 of the oracle) over the whole
+  grid, with the CFL step of each: step sizes within 1e-5, depth within 1e-4
+  (max) and 1e-5 (L2), u and v within 5e-4 / 1e-4 of their scale.
+* River 8192^2: the FP32 GPU step against the oracle on
   crops around sample points, interior, boundaries and corners, with a fixed
   step size.  A cell after K steps depends on cells at most 2 K away, so a
   crop margin of 2 K + 2 cells on its cut sides makes the crop's answer exact
@@ -25,7 +30,7 @@ import numpy as np
 import pytest
 
 from paper_1309_1230_gb300 import inputs as I
-from tests.gpu_util import gpu_solver, oracle_params, rel_depth_err
+from tests.gpu_util import assert_fp32_close, fp32_errors, gpu_solver, oracle_params, rel_depth_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +66,8 @@ def test_dambreak_2048_1000_steps(dambreak_ref, precision, replay, record_proper
     href = ref.eta - case["z"]
     share = float(np.mean(np.abs((e - case["z"]) - href) > 1e-4 * href.max()))
     record_property("share_above_1e-4", share)
+    err = fp32_errors(e, u, v, ref.eta, ref.u, ref.v, case["z"])
+    print("  FP32 errors (max, L2) of h, u, v:", err)
     assert el2 <= 1e-5, el2
     assert share <= 1e-3, share
     assert emax <= 1e-2, emax
@@ -98,3 +105,26 @@ def test_river_8192_sampled_crops(oracle):
         emax, _ = rel_depth_err(hg, hr)
         assert emax <= 1e-4, ((x0, y0), emax)
         assert np.max(np.abs(u[y0:y0 + W, x0:x0 + W] - r.u[w])) <= 1e-4 * max(1.0, np.max(np.abs(r.u[w])))
+
+
+def test_river_8192_500_steps_fp32_against_fp64(record_property):
+    from paper_1309_1230_gb300 import swe
+    case = I.river(8192, 8192)
+    res = {}
+    for prec in (swe.SWE_FP64, swe.SWE_FP32):
+        s = gpu_solver(case, prec, swe.SWE_KERNEL_FUSED)
+        info, dts = s.step(500, want_dt=True)
+        res[prec] = (dts, s.get_state(), info)
+        s.close()
+    d64, (e64, u64, v64), i64 = res[swe.SWE_FP64]
+    d32, (e32, u32, v32), i32 = res[swe.SWE_FP32]
+    del res
+    assert np.isfinite(e32).all() and np.isfinite(u32).all() and np.isfinite(v32).all()
+    assert float(np.max(np.abs(d32 - d64) / d64)) <= 1e-5
+    err = fp32_errors(e32, u32, v32, e64, u64, v64, case["z"])
+    for f in "huv":
+        record_property(f"{f}_rel_max", err[f][0])
+        record_property(f"{f}_rel_l2", err[f][1])
+    print("river 8192^2 x 500, FP32 against FP64:", err)
+    assert_fp32_close(e32, u32, v32, e64, u64, v64, case["z"])
+    assert np.max(np.abs(np.asarray(i32.bflux) - i64.bflux)) <= 1e-4 * np.max(np.abs(i64.bflux))

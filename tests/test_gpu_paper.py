@@ -24,6 +24,7 @@ CASES = {
     "dambreak": (lambda: I.dam_break(260, 90, seed=3), 80),
     "river": (lambda: I.river(300, 70, seed=7), 80),
     "basin_k": (lambda: I.basin_hump(64, 64, manning_n=0.03, kappa=0.25), 60),
+    "aniso_river": (lambda: I.with_cell_size(I.open_river(150, 70, seed=7), 0.7, 1.9), 60),
 }
 
 
