@@ -70,7 +70,7 @@ def test_gpu_adjoint_on_the_512_grid_matches_oracle_adjoint(oracle):
     cells, so 8 gauges within 24 cells of the centre join the 16 uniform ones
     (otherwise no gauge sees moving water and the Manning gradient is zero).
     FP64 against the oracle's adjoint at 1e-10; FP32 against FP64 within
-    1e-3 of each gradient's scale."""
+    2e-4 of each gradient's scale."""
     from paper_1309_1230_gb300 import swe
     c = I.adjoint_case(512, 512)
     T = 120
@@ -95,8 +95,8 @@ def test_gpu_adjoint_on_the_512_grid_matches_oracle_adjoint(oracle):
     for g in (gn, ge):  # neither gradient is trivial: both spread over thousands of cells
         assert np.count_nonzero(np.abs(g) > 1e-6 * np.max(np.abs(g))) > 1000
     l32, gn32, ge32 = res[swe.SWE_FP32]
-    assert l32 == pytest.approx(loss, rel=1e-4)
-    assert _rel(gn32, gn) <= 1e-3 and _rel(ge32, ge) <= 1e-3, (_rel(gn32, gn), _rel(ge32, ge))
+    assert l32 == pytest.approx(loss, rel=1e-5)
+    assert _rel(gn32, gn) <= 2e-4 and _rel(ge32, ge) <= 2e-4, (_rel(gn32, gn), _rel(ge32, ge))
 
 
 def test_gpu_adjoint_matches_central_differences():
@@ -149,9 +149,11 @@ def test_gpu_adjoint_fp32_and_checkpoint_spacing():
     for every in (1, 7):  # same arithmetic, other checkpoints: bitwise
         b = res[(swe.SWE_FP64, every)]
         assert b[0] == a[0] and np.array_equal(b[1], a[1]) and np.array_equal(b[2], a[2])
+    # FP32 against FP64: measured 1.1e-6 (loss), 3.8e-6 (grad n) and 1.8e-5
+    # (grad eta0) here, at most 2.1e-5 up to 512^2 x 400 steps; bounds 10x that
     f = res[(swe.SWE_FP32, 0)]
-    assert f[0] == pytest.approx(a[0], rel=1e-3)
-    assert _rel(f[1], a[1]) <= 2e-2 and _rel(f[2], a[2]) <= 2e-2
+    assert f[0] == pytest.approx(a[0], rel=1e-5)
+    assert _rel(f[1], a[1]) <= 2e-4 and _rel(f[2], a[2]) <= 2e-4
 
 
 def test_autograd_function():

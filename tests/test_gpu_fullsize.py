@@ -4,13 +4,15 @@ times (fused kernel, automatic work plan).
 * Dam break 2048^2, 1000 steps: the FP32 and FP64 GPU steps against the FP64
   oracle over the whole grid (the oracle runs on all host cores), with the
   CFL step and with the oracle's step sizes replayed.  FP64 agrees to 1e-9
-  (measured ~2e-15).  FP32: storing the state in binary32 rounds eta to
-  ~1e-6 m per step; at the moving bores the shock position moves by a
-  fraction of a cell under that noise, so the max-norm error there is the
-  jump times that fraction (measured 2.8e-3 of max depth at ~40 of 4.2 M
-  cells after 1000 steps, the same with IEEE-accurate division, square root
-  and pow).  The bounds below are the relative L2 error (measured 2e-6 to
-  4e-6), the share of cells beyond 1e-4 (measured < 0.02 %) and the max.
+  (measured ~2e-15).  FP32: at the moving wet/dry fronts the max-norm error
+  is 2.8e-3 of max depth at ~40 of 4.2 M cells after 1000 steps.  Storing the
+  state in binary32 is enough to cause it: the FP64 oracle with its state
+  rounded to binary32 after every step moves 39 cells by up to 7.1e-4
+  (oracle/perturbation.py; tests/test_fp32_storage_reading.py shows the same
+  at 384^2 on the CPU), while a one-time rounding of its input moves nothing
+  beyond 1e-7.  So the FP32 run is bounded by the relative L2 error
+  (measured 2e-6 to 4e-6), the share of cells beyond 1e-4 (measured
+  < 0.02 %) and a max of 1e-2.
 * River 8192^2 (the benchmark grid), its full 500 steps: the FP32 GPU step
   against the FP64 GPU step (the fused sweep in FP64, which the tests above
   and the other parity files hold to 1e-10 of the oracle) over the whole
