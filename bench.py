@@ -13,6 +13,13 @@ timed on the host cores on a bounded sample, an end-to-end number through
 the C ABI with pinned host buffers, and SM clock samples taken during the
 timed region.
 
+The line's "forms" object measures the rest of the metric in the same
+process (rank 0): the same river in FP64 (the fused sweep and the plain
+two-kernel step), the 256-scenario batched ensemble (1000 steps in one
+persistent graph-captured launch, with and without the dry-item skip) and
+the discrete adjoint's cost against a forward run (512^2, 2000 steps, FP64
+and FP32), with its own clock samples.
+
 --impl reference times the FP64 CPU oracle on the host cores (bounded crop
 of the same workload) and prints the same line with "impl": "reference".
 Multi-GPU (torchrun, N ranks): N independent replicas, one per GPU
@@ -101,7 +108,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -178,6 +185,131 @@ def job_rate(cells_per_rank: int, steps: int, local_ms: float, dist=None):
     return world * cells_per_rank * steps / (ms / 1e3), ms
 
 
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_fp64_steps(case, steps: int, device: int) -> dict:
+    """The same river in FP64: the fused sweep and the plain one-thread-per-cell
+    step (two kernels per step), each timed with CUDA events on its stream."""
+    import torch
+    from paper_1309_1230_gb300 import swe
+    out = {}
+    for name, kern in (("fused", swe.SWE_KERNEL_FUSED), ("plain", swe.SWE_KERNEL_PLAIN)):
+        s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=case["kappa"], bc=case["bc"],
+                       q_in=case["q_in"], precision=swe.SWE_FP64, kernel=kern, device=device)
+        s.set_bed(case["z"])
+        s.set_state(case["eta"], case["u"], case["v"])
+        st = torch.cuda.ExternalStream(s.stream_handle(), device=device)
+        s.step(2, want_info=False)
+        e0, e1 = _events(st)
+        torch.cuda.synchronize()
+        e0.record(st)
+        s.step(steps, want_info=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        cells = case["nx"] * case["ny"]
+        out[name] = {"ms_per_step": ms, "value": cells / (ms / 1e3), "steps": steps}
+        s.close()
+    out["unit"] = METRIC
+    out["workload"] = "the same river reach 8192x8192, FP64 state and arithmetic"
+    out["roofline"] = {"bound": "fp64 alu", "note": "56 B/cell of state traffic; GB300's FP64 rate (~1.25 TFLOP/s) "
+                       "bounds it, not HBM"}
+    return out
+
+
+def bench_batched(steps: int, device: int) -> dict:
+    """The ensemble form: 256 dam breaks of uneven size (Nx, Ny ~ U{128..1024}),
+    FP32, `steps` steps in one persistent cooperative launch captured in a CUDA
+    graph; timed with CUDA events on the batch's stream, with the dry-item skip
+    (default) and without it.  Every cell of every scenario counts."""
+    import torch
+    from paper_1309_1230_gb300 import inputs as I
+    from paper_1309_1230_gb300 import swe
+    cases = I.ensemble(256)
+    cells = sum(c["nx"] * c["ny"] for c in cases)
+    st = torch.cuda.Stream(device=device)
+    peaks = measured_peaks()
+    out = {"workload": "256 dam-break scenarios, Nx, Ny ~ U{128..1024}, n ~ U(0.01,0.05), H ~ U(2,10) m, "
+                       "dry right half, FP32, one persistent graph-captured launch per call",
+           "scenarios": len(cases), "cells": cells, "steps": steps, "unit": METRIC}
+    for skip in (1, 0):
+        b = swe.Batch([(c["nx"], c["ny"]) for c in cases], [c["manning_n"] for c in cases], kappa=cases[0]["kappa"],
+                      dry_skip=skip, stream=st.cuda_stream, device=device)
+        for i, c in enumerate(cases):
+            b.set_bed(i, c["z"])
+            b.set_state(i, c["eta"], c["u"], c["v"])
+        b.step(steps, want_info=False)  # the first call of this length captures its graph
+        for i, c in enumerate(cases):
+            b.set_state(i, c["eta"], c["u"], c["v"])
+        e0, e1 = _events(st)
+        torch.cuda.synchronize()
+        e0.record(st)
+        b.step(steps, want_info=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rate = cells * steps / (ms / 1e3)
+        achieved = BYTES_PER_CELL_FP32 * rate / 1e9
+        key = "dry_skip" if skip else "no_dry_skip"
+        out[key] = {"value": rate, "ms_per_call": ms, "rows_per_item": int(b.params.seg_rows) or 192,
+                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": achieved / peaks["hbm_gbs"], "bytes_per_cell": BYTES_PER_CELL_FP32,
+                                 "note": "algorithmic bytes of every cell, skipped dry cells included"
+                                 if skip else "algorithmic bytes of every cell"}}
+        b.close()
+    out["value"] = out["dry_skip"]["value"]
+    return out
+
+
+def bench_adjoint(T: int, device: int) -> dict:
+    """Cost of the discrete adjoint on the 512^2 adjoint workload: one
+    swe_adjoint call over T steps (its own forward run with sqrt(T)
+    checkpoints, the recomputation and the reverse sweep) against a plain
+    T-step forward of the same context, wall clock with the device
+    synchronised on both sides, FP64 and FP32.  The gauge records are
+    synthetic (the cost does not depend on them)."""
+    import numpy as np
+    import torch
+    from paper_1309_1230_gb300 import inputs as I
+    from paper_1309_1230_gb300 import swe
+    c = I.adjoint_case(512, 512)
+    rng = np.random.Generator(np.random.PCG64(5))
+    obs = c["eta"].ravel()[c["gauges"]][None, :] + 0.01 * rng.standard_normal((T, len(c["gauges"])))
+    out = {"workload": f"adjoint: 512x512, {T} steps, 16 gauges, kappa 0, gradient w.r.t. n and eta0, "
+                       f"ceil(sqrt(T)) = {int(np.ceil(np.sqrt(T)))} checkpoints", "steps": T}
+    for name, prec in (("fp64", swe.SWE_FP64), ("fp32", swe.SWE_FP32)):
+        def fresh():
+            s = swe.Solver(512, 512, manning_n=0.03, kappa=0.0, precision=prec, device=device)
+            s.set_bed(c["z"], np.full((512, 512), 0.03))
+            s.set_state(c["eta"], c["u"], c["v"])
+            return s
+        s = fresh()
+        s.step(T, want_info=False)  # warm-up: graphs captured, kernels loaded
+        s.set_state(c["eta"], c["u"], c["v"])
+        s.set_clock(0, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(T, want_info=False)
+        torch.cuda.synchronize()
+        fwd = time.perf_counter() - t0
+        s.close()
+        s = fresh()
+        s.adjoint(T, c["gauges"], obs)  # warm-up
+        s.set_state(c["eta"], c["u"], c["v"])
+        s.set_clock(0, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.adjoint(T, c["gauges"], obs)
+        torch.cuda.synchronize()
+        adj = time.perf_counter() - t0
+        s.close()
+        out[name] = {"forward_s": fwd, "adjoint_s": adj, "cost_ratio": adj / fwd}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -207,6 +339,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64, batched and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -293,6 +426,16 @@ def main():
         cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
                "sample": f"FP64 oracle, 4096x4096 west-end window of the workload, 60 steps ({secs:.1f} s)"}
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        with ClockSampler(local) as fclk:
+            forms = {"fp32_step": {"value": value, "ms_per_step": ms / args.steps, "unit": METRIC},
+                     "fp64_step": bench_fp64_steps(case, 5, local),
+                     "batched": bench_batched(1000, local),
+                     "adjoint": bench_adjoint(2000, local)}
+        forms["fp64_step"]["fp32_over_fp64_fused"] = value / forms["fp64_step"]["fused"]["value"]
+        forms["clocks"] = fclk.summary()
+
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -303,7 +446,7 @@ def main():
                        "rows_per_item": tuned_rows,
                        "autotune_ms_per_step": {str(k): round(v, 4) for k, v in tune_table.items()},
                        "t_end_s": info.t, "dt_last_s": info.dt_last},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                        "samples": clocks["samples"]},
             "gpu_launches": args.steps + 1}

@@ -4,6 +4,10 @@ Used for profiler captures and quick throughput checks, e.g.
 
     python -m paper_1309_1230_gb300.run_case --case river --n 4096 --steps 4
     python -m paper_1309_1230_gb300.run_case --case dambreak --n 2048 --precision fp64 --kernel plain
+    python -m paper_1309_1230_gb300.run_case --case ensemble --count 64 --steps 100
+
+(the ensemble case runs the batched FP32 form: --count dam breaks with sides
+U{128..min(n, 1024)}, all --steps in one persistent launch)
 
 Prints one line with the step time measured with CUDA events.
 """
@@ -16,7 +20,8 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="river", choices=["river", "dambreak", "basin"])
+    ap.add_argument("--case", default="river", choices=["river", "dambreak", "basin", "ensemble"])
+    ap.add_argument("--count", type=int, default=256, help="ensemble: number of scenarios")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=2)
@@ -31,6 +36,8 @@ def main(argv=None):
     from . import inputs as I
     from . import swe
 
+    if a.case == "ensemble":
+        return run_ensemble(a)
     if a.case == "river":
         case = I.river(a.n, a.n)
     elif a.case == "dambreak":
@@ -59,6 +66,33 @@ def main(argv=None):
                       "ms_per_step": ms, "cell_updates_per_s": case["nx"] * case["ny"] / (ms / 1e3),
                       "volume": info.volume, "t": info.t, "time": time.time()}))
     s.close()
+
+
+def run_ensemble(a):
+    import torch
+
+    from . import inputs as I
+    from . import swe
+
+    cases = I.ensemble(a.count, side=(128, min(max(a.n, 128), 1024)))
+    st = torch.cuda.Stream()
+    b = swe.Batch([(c["nx"], c["ny"]) for c in cases], [c["manning_n"] for c in cases], kappa=cases[0]["kappa"],
+                  seg_rows=a.seg_rows, dry_skip=a.dry_skip, stream=st.cuda_stream)
+    for i, c in enumerate(cases):
+        b.set_bed(i, c["z"])
+        b.set_state(i, c["eta"], c["u"], c["v"])
+    b.step(a.warmup, want_info=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    b.step(a.steps, want_info=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = sum(c["nx"] * c["ny"] for c in cases)
+    print(json.dumps({"case": "ensemble", "count": a.count, "cells": cells, "steps": a.steps, "dry_skip": a.dry_skip,
+                      "ms_per_call": ms, "cell_updates_per_s": cells * a.steps / (ms / 1e3), "time": time.time()}))
+    b.close()
 
 
 if __name__ == "__main__":
