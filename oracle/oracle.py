@@ -139,7 +139,7 @@ class OracleLib:
         if hasattr(lib, "orc_adjoint"):
             lp = ctypes.POINTER(ctypes.c_int64)
             lib.orc_adjoint.argtypes = [P, dp, dp, dp, dp, dp, ctypes.c_int64, ctypes.c_int32, dp, lp,
-                                        ctypes.c_int32, dp, dp, dp, dp, dp, dp]
+                                        ctypes.c_int32, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_adjoint.restype = ctypes.c_int
         self.lib = lib
 
@@ -189,9 +189,10 @@ class OracleLib:
 
 
 class AdjointResult:
-    def __init__(self, loss, grad_n, grad_eta0, grad_u0, grad_v0, status):
+    def __init__(self, loss, grad_n, grad_eta0, grad_u0, grad_v0, status, grad_z=None):
         self.loss, self.grad_n, self.grad_eta0 = loss, grad_n, grad_eta0
         self.grad_u0, self.grad_v0, self.status = grad_u0, grad_v0, status
+        self.grad_z = grad_z
 
 
 def _adjoint(lib, p, z, nfield, eta, u, v, dt, gauges, obs, step0=0):
@@ -203,14 +204,14 @@ def _adjoint(lib, p, z, nfield, eta, u, v, dt, gauges, obs, step0=0):
     g = np.ascontiguousarray(gauges, dtype=np.int64)
     ob = np.ascontiguousarray(obs, dtype=np.float64).reshape(T, g.shape[0])
     loss = np.zeros(1)
-    gn, ge, gu, gv = (np.zeros(shape) for _ in range(4))
+    gn, ge, gu, gv, gz = (np.zeros(shape) for _ in range(5))
     pc = p._c()
     st = lib.orc_adjoint(ctypes.byref(pc), _ptr(z), _ptr(nf), _ptr(e), _ptr(uu), _ptr(vv), int(step0), int(T),
                          _ptr(dt), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(g.shape[0]), _ptr(ob),
-                         _ptr(loss), _ptr(gn), _ptr(ge), _ptr(gu), _ptr(gv))
+                         _ptr(loss), _ptr(gn), _ptr(ge), _ptr(gu), _ptr(gv), _ptr(gz))
     if st == 1:
         raise ValueError("oracle rejected the adjoint arguments")
-    return AdjointResult(float(loss[0]), gn, ge, gu, gv, st)
+    return AdjointResult(float(loss[0]), gn, ge, gu, gv, st, gz)
 
 
 OracleLib.adjoint = lambda self, *a, **k: _adjoint(self.lib, *a, **k)
@@ -245,5 +246,6 @@ def prepare_state(p: Params, z, eta, u, v):
 def adjoint(p: Params, z, nfield, eta, u, v, dt, gauges, obs, step0: int = 0) -> AdjointResult:
     """Discrete adjoint of nsteps = len(dt) steps with frozen step sizes:
     gradient of L = 1/2 sum_k sum_g (eta_g^k - obs[k-1, g])^2 with respect to
-    the per-cell Manning n and the initial eta, u, v (kappa 0, fully wet)."""
+    the per-cell Manning n, the bed z and the initial eta, u, v (kappa 0,
+    fully wet)."""
     return _default().adjoint(p, z, nfield, eta, u, v, dt, gauges, obs, step0)

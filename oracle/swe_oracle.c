@@ -578,11 +578,12 @@ typedef struct {
     double *les, *lus, *lvs, *lhs;    /* predicted (with ghosts) */
     double *lCs, *lfxs, *lfys, *lqxs, *lqys;
     double *ln2;                      /* per cell */
+    double *lz;                       /* per cell: cotangent of the bed z of this step */
 } adjw;
 
 static void adjw_free(adjw* a) {
     void* ptrs[] = {a->le, a->lu, a->lv, a->lh, a->lC, a->lfx, a->lfy, a->lqx, a->lqy, a->les, a->lus,
-                    a->lvs, a->lhs, a->lCs, a->lfxs, a->lfys, a->lqxs, a->lqys, a->ln2};
+                    a->lvs, a->lhs, a->lCs, a->lfxs, a->lfys, a->lqxs, a->lqys, a->ln2, a->lz};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     memset(a, 0, sizeof(*a));
 }
@@ -592,7 +593,7 @@ static int adjw_alloc(adjw* a, int nx, int ny) {
     size_t nc = (size_t)(nx + 2) * (size_t)(ny + 2);
     size_t nfx = (size_t)(nx + 1) * (size_t)ny, nfy = (size_t)nx * (size_t)(ny + 1);
     double** cells[] = {&a->le, &a->lu, &a->lv, &a->lh, &a->lC, &a->lqx, &a->lqy, &a->les, &a->lus,
-                        &a->lvs, &a->lhs, &a->lCs, &a->lqxs, &a->lqys, &a->ln2};
+                        &a->lvs, &a->lhs, &a->lCs, &a->lqxs, &a->lqys, &a->ln2, &a->lz};
     for (size_t k = 0; k < sizeof(cells) / sizeof(cells[0]); ++k)
         if (!(*cells[k] = calloc(nc, sizeof(double)))) { adjw_free(a); return 0; }
     if (!(a->lfx = calloc(nfx, sizeof(double))) || !(a->lfy = calloc(nfy, sizeof(double))) ||
@@ -832,7 +833,7 @@ static void adj_step(const orc_params* p, work* w, adjw* a, double dt, int sx, i
     adj_ghosts(p, w, w->hs, a->les, a->lus, a->lvs, a->lhs);
     /* S8: the fix is the identity (wet, no clamp); h* = eta* - z */
     for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->les[c] += a->lhs[c]; }
+        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->les[c] += a->lhs[c]; a->lz[c] -= a->lhs[c]; }
     /* S7: predictor momentum (differenced and base state: level n) */
     adj_momentum(p, w, dt, sx, sy, w->eta, w->u, w->v, w->wet, w->C, w->us, w->vs, a->lus, a->lvs,
                  a->le, a->lu, a->lv, a->lC, a->lu, a->lv);
@@ -846,19 +847,21 @@ static void adj_step(const orc_params* p, work* w, adjw* a, double dt, int sx, i
     adj_ghosts(p, w, w->h, a->le, a->lu, a->lv, a->lh);
     /* S1: h = eta - z */
     for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->le[c] += a->lh[c]; }
+        for (int i = 0; i < nx; ++i) { size_t c = G(i, j); a->le[c] += a->lh[c]; a->lz[c] -= a->lh[c]; }
     free(less); free(luss); free(lvss);
 }
 
 /* Gradient of L = 1/2 sum_{k=1..T} sum_g (eta_g^k - obs[k-1][g])^2 with
- * respect to the per-cell Manning n field and the initial eta (and u, v),
- * by the discrete adjoint of T steps from step index step0 with the given
- * frozen step sizes.  Returns 0, 1 (bad argument), 3 (non-finite) or 5 (a
- * stage was not fully wet, or kappa != 0). */
+ * respect to the per-cell Manning n field, the bed elevation z (which enters
+ * every stage through the depth h = eta - z, and the ghost cells through
+ * their copy of the adjacent bed) and the initial eta (and u, v), by the
+ * discrete adjoint of T steps from step index step0 with the given frozen
+ * step sizes.  Returns 0, 1 (bad argument), 3 (non-finite) or 5 (a stage was
+ * not fully wet, or kappa != 0). */
 int orc_adjoint(const orc_params* p, const double* z, const double* nfield, const double* eta0,
                 const double* u0, const double* v0, int64_t step0, int32_t T, const double* dt,
                 const int64_t* gauges, int32_t ng, const double* obs, double* loss, double* grad_n,
-                double* grad_eta0, double* grad_u0, double* grad_v0) {
+                double* grad_eta0, double* grad_u0, double* grad_v0, double* grad_z) {
     if (!check_params(p) || !z || !nfield || !eta0 || !u0 || !v0 || !dt || T < 0 || ng < 0 || !loss) return ORC_ERR_ARG;
     if (p->kappa != 0.0) return ORC_ERR_NOT_WET;
     const int nx = p->nx, ny = p->ny;
@@ -873,7 +876,8 @@ int orc_adjoint(const orc_params* p, const double* z, const double* nfield, cons
     double* st = malloc((size_t)(T + 1) * 3 * n * sizeof(double));
     double *le1 = malloc(n * sizeof(double)), *lu1 = malloc(n * sizeof(double)), *lv1 = malloc(n * sizeof(double));
     double* gn = calloc(nc, sizeof(double));
-    if (!st || !le1 || !lu1 || !lv1 || !gn) { free(st); free(le1); free(lu1); free(lv1); free(gn); adjw_free(a); work_free(w); return ORC_ERR_ARG; }
+    double* gz = calloc(nc, sizeof(double));
+    if (!st || !le1 || !lu1 || !lv1 || !gn || !gz) { free(st); free(le1); free(lu1); free(lv1); free(gn); free(gz); adjw_free(a); work_free(w); return ORC_ERR_ARG; }
     load(p, w, z, nfield, eta0, u0, v0);
     int rc = ORC_OK;
     double L = 0.0;
@@ -918,8 +922,9 @@ int orc_adjoint(const orc_params* p, const double* z, const double* nfield, cons
             int sx, sy;
             fwd_keep(p, w, step0 + s, dt[s], &sx, &sy);
             memset(a->ln2, 0, nc * sizeof(double));
+            memset(a->lz, 0, nc * sizeof(double));
             adj_step(p, w, a, dt[s], sx, sy, le1, lu1, lv1);
-            for (size_t c = 0; c < nc; ++c) gn[c] += a->ln2[c];
+            for (size_t c = 0; c < nc; ++c) { gn[c] += a->ln2[c]; gz[c] += a->lz[c]; }
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
                     size_t c = G(i, j), k = (size_t)j * nx + i;
@@ -936,9 +941,10 @@ int orc_adjoint(const orc_params* p, const double* z, const double* nfield, cons
                 if (grad_eta0) grad_eta0[k] = le1[k];
                 if (grad_u0) grad_u0[k] = lu1[k];
                 if (grad_v0) grad_v0[k] = lv1[k];
+                if (grad_z) grad_z[k] = gz[c];
             }
     }
-    free(st); free(le1); free(lu1); free(lv1); free(gn);
+    free(st); free(le1); free(lu1); free(lv1); free(gn); free(gz);
     adjw_free(a);
     work_free(w);
     return rc;

@@ -1,7 +1,7 @@
 """Pins of the oracle's discrete adjoint: central finite differences of the
 oracle's own forward map (the gradient is the directional derivative), in
-random directions of the Manning field and the initial state, plus its
-scope checks.  FP64, frozen step sizes, kappa = 0, fully wet."""
+random directions of the Manning field, the bed and the initial state, plus
+its scope checks.  FP64, frozen step sizes, kappa = 0, fully wet."""
 from __future__ import annotations
 
 import numpy as np
@@ -19,14 +19,15 @@ def _case(nx=24, ny=20, T=30, seed=4, bc=(0, 0, 0, 0), q_in=(0.0,) * 4):
     return c, nfield, T, bc, q_in
 
 
-def _loss(O, p, c, nfield, eta, u, v, dt, gauges, obs):
-    r = O.run(p, c["z"], eta, u, v, len(dt), nfield=nfield, dt_fixed=dt)
+def _loss(O, p, c, nfield, eta, u, v, dt, gauges, obs, z=None):
+    z = c["z"] if z is None else z
+    r = O.run(p, z, eta, u, v, len(dt), nfield=nfield, dt_fixed=dt)
     assert r.status == 0
     # re-run step by step to collect the gauge series (oracle forward only)
     L = 0.0
     e, uu, vv = eta, u, v
     for k in range(len(dt)):
-        r = O.run(p, c["z"], e, uu, vv, 1, nfield=nfield, dt_fixed=dt[k:k + 1], step0=k)
+        r = O.run(p, z, e, uu, vv, 1, nfield=nfield, dt_fixed=dt[k:k + 1], step0=k)
         e, uu, vv = r.eta, r.u, r.v
         res = e.ravel()[gauges] - obs[k]
         L += 0.5 * float(res @ res)
@@ -57,6 +58,33 @@ def test_adjoint_matches_central_differences(oracle, bcs):
         fd = (Lp - Lm) / (2 * eps)
         ad = float(np.sum(adj.grad_n * dn) + np.sum(adj.grad_eta0 * de) + np.sum(adj.grad_u0 * du))
         assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-12), (trial, fd, ad)
+    # the bed alone, with the initial elevation held (so the depth changes)
+    for trial in range(3):
+        dz = rng.standard_normal(nfield.shape) * 0.01
+        eps = 1e-5
+        Lp = _loss(oracle, p, c, nfield, c["eta"], c["u"], c["v"], dt, gauges, obs, z=c["z"] + eps * dz)
+        Lm = _loss(oracle, p, c, nfield, c["eta"], c["u"], c["v"], dt, gauges, obs, z=c["z"] - eps * dz)
+        fd = (Lp - Lm) / (2 * eps)
+        ad = float(np.sum(adj.grad_z * dz))
+        assert abs(fd) > 0.0
+        assert abs(fd - ad) <= 1e-5 * abs(fd), ("bed", trial, fd, ad)
+
+
+def test_bed_gradient_of_a_lake_at_rest_is_zero(oracle):
+    """A lake at rest (flat surface, zero velocity) stays at rest over any
+    fully submerged bed, so the loss does not depend on the bed to first
+    order: with gauge records 1 cm off the surface (nonzero residuals) the
+    bed and Manning gradients are exactly zero while the gradient with
+    respect to the initial surface is not."""
+    c, nfield, T, bc, q = _case(T=12)
+    eta = np.full_like(c["eta"], float(c["z"].max()) + 1.0)
+    zero = np.zeros_like(eta)
+    p = oracle.Params(nx=c["nx"], ny=c["ny"], manning_n=0.03, kappa=0.0)
+    obs = np.full((T, len(c["gauges"])), eta[0, 0] + 0.01)
+    adj = oracle.adjoint(p, c["z"], nfield, eta, zero, zero, np.full(T, 0.05), c["gauges"], obs)
+    assert adj.status == 0 and adj.loss > 0.0
+    assert np.abs(adj.grad_eta0).max() > 0.0
+    assert not adj.grad_z.any() and not adj.grad_n.any()
 
 
 def test_adjoint_scope_is_enforced(oracle):
