@@ -83,7 +83,13 @@ typedef enum {
      * it on the GPU.  With the same step sizes the state equals the other
      * kernels' bit for bit.  No adjoint (SWE_ERR_UNSUPPORTED). */
     SWE_KERNEL_PAPER = 2,
-    SWE_KERNEL_PAPER_DEVDT = 3
+    SWE_KERNEL_PAPER_DEVDT = 3,
+    /* The paper's shared-memory design (Sec. 3.2): as SWE_KERNEL_PAPER(_DEVDT),
+     * but the sub-steps that read neighbours run in 16 x 16 thread blocks with
+     * the block's cells and halo staged in shared memory.  Same results bit
+     * for bit. */
+    SWE_KERNEL_PAPER_SHARED = 4,
+    SWE_KERNEL_PAPER_SHARED_DEVDT = 5
 } swe_kernel;
 
 /* Step-info flag bits */
@@ -211,8 +217,11 @@ void swe_destroy(swe_ctx* ctx);
  * loss L = 1/2 sum_{k=1..nsteps} sum_g (eta_g^k - obs[(k-1)*ngauges + g])^2 at
  * the gauge cells gauges[g] (index j*nx+i), and its gradient with respect to
  * the per-cell Manning n (grad_n, host, ny*nx; the uniform manning_n counts
- * as a field) and to the initial elevation (grad_eta0, host, ny*nx); both
- * nullable.  The step sizes are those of the forward run and are held fixed
+ * as a field), to the initial elevation (grad_eta0, host, ny*nx) and to the
+ * bed elevation (grad_z, host, ny*nx, with the initial elevation held, so
+ * that a bed change is a depth change); all three nullable.  The paper has no
+ * adjoint: this differentiates the step of Sec. 1 with the step sizes of
+ * Sec. 3.1 held at the forward run's.  The step sizes are those of the forward run and are held fixed
  * (the CFL minimum is not differentiated).  Requires kappa = 0
  * (SWE_ERR_UNSUPPORTED otherwise); the derivative is that of the smooth,
  * fully wet branch of the wet/dry fixes.  The forward states are kept every
@@ -220,7 +229,7 @@ void swe_destroy(swe_ctx* ctx);
  * Advances the context by nsteps steps (the forward run) and allocates its
  * working buffers for the duration of the call. */
 swe_status swe_adjoint(swe_ctx* ctx, int32_t nsteps, const int64_t* gauges, int32_t ngauges, const double* obs,
-                       int32_t checkpoint_every, double* loss, double* grad_n, double* grad_eta0);
+                       int32_t checkpoint_every, double* loss, double* grad_n, double* grad_eta0, double* grad_z);
 
 /* Work-item autotuner of the fused step (the kernel's only shape parameter is
  * the number of rows per work item, seg_rows; an item is one warp's column

@@ -5,6 +5,11 @@
 // The step is differentiated with its step size frozen (the CFL minimum is
 // not differentiable) and in the regime where it is smooth: no dissipation
 // (kappa = 0) and every cell wet, so the wet/dry fixes are the identity.
+// The bed elevation enters the step only through the depth h = eta - z (and
+// the ghost cells' copy of the adjacent bed), so every cotangent record below
+// keeps the part that reached a cell through its depth (h) apart from the
+// part that reached its elevation directly (e): the cotangent of eta is
+// e + h, that of the bed is -h.
 // One reverse step, for the level-n state q^n and the cotangent lambda of
 // level n+1:
 //   1. recompute the predicted state q* (the plain predictor kernel);
@@ -38,20 +43,28 @@ struct Vjp3 {
     T e, u, v;
 };
 
-// Cotangent of ghost(in, side) folded into the cotangent of `in`.
+// Cotangent of a cell: elevation (direct), velocities, and depth.
 template <class T>
-__device__ __forceinline__ void ghost_vjp(const Cell<T>& in, int side, const GridK<T>& G, const Vjp3<T>& lg,
-                                          Vjp3<T>& li) {
+struct Vjp4 {
+    T e, u, v, h;
+};
+
+// Cotangent of ghost(in, side) folded into the cotangent of `in` (the ghost
+// copies the cell's elevation and bed, hence its depth).
+template <class T>
+__device__ __forceinline__ void ghost_vjp(const Cell<T>& in, int side, const GridK<T>& G, const Vjp4<T>& lg,
+                                          Vjp4<T>& li) {
     li.e += lg.e;
+    li.h += lg.h;
     const int bc = G.bc[side];
     const bool xs = side < 2;
     if (bc == BC_WALL) {
         if (xs) { li.u -= lg.u; li.v += lg.v; } else { li.u += lg.u; li.v -= lg.v; }
     } else if (bc == BC_INFLOW) {
         const T h = in.e - in.z;
-        if (h > G.h_dry) {
+        if (h > G.h_dry) {  // the ghost velocity q_in / h
             const T sgn = (side == SIDE_W || side == SIDE_S) ? T(1) : T(-1);
-            li.e += -sgn * G.qin[side] / (h * h) * (xs ? lg.u : lg.v);
+            li.h += -sgn * G.qin[side] / (h * h) * (xs ? lg.u : lg.v);
         }
     } else {
         li.u += lg.u; li.v += lg.v;
@@ -64,8 +77,8 @@ __device__ __forceinline__ void ghost_vjp(const Cell<T>& in, int side, const Gri
 // level-n base values and g n^2.
 template <int DX, int DY, class T>
 __device__ __forceinline__ void stage_vjp(const Cell<T>& c, const Cell<T>& xn, const Cell<T>& yn, T e0, T u0, T v0,
-                                          T gn2, const StepK<T>& S, T h_dry, T le, T lu, T lv, Vjp3<T>& lc,
-                                          Vjp3<T>& lx, Vjp3<T>& ly, T (&lf)[4], Vjp3<T>& lb, T& lgn2) {
+                                          T gn2, const StepK<T>& S, T h_dry, T le, T lu, T lv, Vjp4<T>& lc,
+                                          Vjp4<T>& lx, Vjp4<T>& ly, T (&lf)[4], Vjp3<T>& lb, T& lgn2) {
     // forward values
     const T h = c.e - c.z;
     const bool wet = h > h_dry;
@@ -112,7 +125,7 @@ __device__ __forceinline__ void stage_vjp(const Cell<T>& c, const Cell<T>& xn, c
             lc.u += gn2 * (c.u / mag) * P * lcf;
             lc.v += gn2 * (c.v / mag) * P * lcf;
         }
-        lc.e += T(-4) / T(3) * cf / h * lcf;
+        lc.h += T(-4) / T(3) * cf / h * lcf;
     }
 }
 
@@ -121,8 +134,8 @@ __device__ __forceinline__ void stage_vjp(const Cell<T>& c, const Cell<T>& xn, c
 // their eta and velocity (flux = (eta - z) * velocity).
 template <int DX, int DY, class T>
 __device__ __forceinline__ void faces_vjp(int i, int j, const GridK<T>& G, const Cell<T>& c, const Cell<T>& xn,
-                                          const Cell<T>& yn, const T (&lf)[4], Vjp3<T>& lc, Vjp3<T>& lx,
-                                          Vjp3<T>& ly) {
+                                          const Cell<T>& yn, const T (&lf)[4], Vjp4<T>& lc, Vjp4<T>& lx,
+                                          Vjp4<T>& ly) {
     T lqc_x = T(0), lqn_x = T(0), lqc_y = T(0), lqn_y = T(0);
     // east / north faces
     if (i == G.nx - 1) { if (G.bc[SIDE_E] == BC_OUTFLOW) lqc_x += lf[0]; }
@@ -133,12 +146,12 @@ __device__ __forceinline__ void faces_vjp(int i, int j, const GridK<T>& G, const
     else if (DY > 0) lqn_y += lf[2]; else lqc_y += lf[2];
     if (j == 0) { if (G.bc[SIDE_S] == BC_OUTFLOW) lqc_y += lf[3]; }
     else if (DY > 0) lqc_y += lf[3]; else lqn_y += lf[3];
-    lc.e += c.u * lqc_x + c.v * lqc_y;
+    lc.h += c.u * lqc_x + c.v * lqc_y;
     lc.u += (c.e - c.z) * lqc_x;
     lc.v += (c.e - c.z) * lqc_y;
-    lx.e += xn.u * lqn_x;
+    lx.h += xn.u * lqn_x;
     lx.u += (xn.e - xn.z) * lqn_x;
-    ly.e += yn.v * lqn_y;
+    ly.h += yn.v * lqn_y;
     ly.v += (yn.e - yn.z) * lqn_y;
 }
 
@@ -154,11 +167,21 @@ struct Planes3 {
     T* e; T* u; T* v;
 };
 
+template <class T>
+struct Planes4 {
+    T* e; T* u; T* v; T* h;
+};
+
+template <class T>
+__device__ __forceinline__ void put4(const Planes4<T>& P, size_t k, const Vjp4<T>& a) {
+    P.e[k] = a.e; P.u[k] = a.u; P.v[k] = a.v; P.h[k] = a.h;
+}
+
 // Step 2: corrector stage VJP (directions -SX, -SY) at every cell.
 template <class T, int SX, int SY>
 __global__ void __launch_bounds__(256) k_adj_corr(GridK<T> G, StepK<T> S, const T* __restrict__ z,
                                                   const T* __restrict__ n2, Planes3<T> qn, Planes3<T> qs,
-                                                  Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX, Planes3<T> GY,
+                                                  Planes3<T> lam, Planes4<T> Sc, Planes4<T> GX, Planes4<T> GY,
                                                   Planes3<T> Bc, T* __restrict__ ggn2, unsigned* dry) {
     constexpr int CX = -SX, CY = -SY;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -173,15 +196,16 @@ __global__ void __launch_bounds__(256) k_adj_corr(GridK<T> G, StepK<T> S, const 
                           : cell_at(qs.e, qs.u, qs.v, z, (size_t)((ptrdiff_t)k + (ptrdiff_t)CY * G.pitch));
     const T gn2 = n2 ? n2[k] : G.gn2;
     const T le = T(0.5) * lam.e[k], lu = T(0.5) * lam.u[k], lv = T(0.5) * lam.v[k];
-    Vjp3<T> lc{le, lu, lv}, lx{0, 0, 0}, ly{0, 0, 0}, lb{0, 0, 0};  // averaging passes half to q* directly
+    Vjp4<T> lc{le, lu, lv, 0}, lx{0, 0, 0, 0}, ly{0, 0, 0, 0};  // averaging passes half to q* directly
+    Vjp3<T> lb{0, 0, 0};
     T lf[4] = {0, 0, 0, 0}, lg = T(0);
     stage_vjp<CX, CY>(cs, xs, ys, qn.e[k], qn.u[k], qn.v[k], gn2, S, G.h_dry, le, lu, lv, lc, lx, ly, lf, lb, lg);
     faces_vjp<CX, CY>(i, j, G, cs, xs, ys, lf, lc, lx, ly);
-    if (gx) { ghost_vjp(cs, sidex, G, lx, lc); lx = Vjp3<T>{0, 0, 0}; }
-    if (gy) { ghost_vjp(cs, sidey, G, ly, lc); ly = Vjp3<T>{0, 0, 0}; }
-    Sc.e[k] = lc.e; Sc.u[k] = lc.u; Sc.v[k] = lc.v;
-    GX.e[k] = lx.e; GX.u[k] = lx.u; GX.v[k] = lx.v;
-    GY.e[k] = ly.e; GY.u[k] = ly.u; GY.v[k] = ly.v;
+    if (gx) { ghost_vjp(cs, sidex, G, lx, lc); lx = Vjp4<T>{0, 0, 0, 0}; }
+    if (gy) { ghost_vjp(cs, sidey, G, ly, lc); ly = Vjp4<T>{0, 0, 0, 0}; }
+    put4(Sc, k, lc);
+    put4(GX, k, lx);
+    put4(GY, k, ly);
     Bc.e[k] = lb.e; Bc.u[k] = lb.u; Bc.v[k] = lb.v;
     ggn2[k] += lg;
 }
@@ -189,22 +213,26 @@ __global__ void __launch_bounds__(256) k_adj_corr(GridK<T> G, StepK<T> S, const 
 // Step 3: gather the cotangent of q*, then the predictor stage VJP.
 template <class T, int SX, int SY>
 __global__ void __launch_bounds__(256) k_adj_pred(GridK<T> G, StepK<T> S, const T* __restrict__ z,
-                                                  const T* __restrict__ n2, Planes3<T> qn, Planes3<T> Sc,
-                                                  Planes3<T> GX, Planes3<T> GY, Planes3<T> Bc, Planes3<T> Pc,
-                                                  Planes3<T> PX, Planes3<T> PY, T* __restrict__ ggn2, unsigned* dry) {
+                                                  const T* __restrict__ n2, Planes3<T> qn, Planes4<T> Sc,
+                                                  Planes4<T> GX, Planes4<T> GY, Planes3<T> Bc, Planes4<T> Pc,
+                                                  Planes4<T> PX, Planes4<T> PY, T* __restrict__ ggn2,
+                                                  T* __restrict__ ggz, unsigned* dry) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const size_t k = (size_t)j * G.pitch + i;
     // the corrector of cell m reads q* of m - SX and m - SY (its upwind side)
-    T ls_e = Sc.e[k], ls_u = Sc.u[k], ls_v = Sc.v[k];
+    T ls_e = Sc.e[k], ls_u = Sc.u[k], ls_v = Sc.v[k], ls_h = Sc.h[k];
     if (i + SX >= 0 && i + SX < G.nx) {
         const size_t m = (size_t)((ptrdiff_t)k + SX);
-        ls_e += GX.e[m]; ls_u += GX.u[m]; ls_v += GX.v[m];
+        ls_e += GX.e[m]; ls_u += GX.u[m]; ls_v += GX.v[m]; ls_h += GX.h[m];
     }
     if (j + SY >= 0 && j + SY < G.ny) {
         const size_t m = (size_t)((ptrdiff_t)k + (ptrdiff_t)SY * G.pitch);
-        ls_e += GY.e[m]; ls_u += GY.u[m]; ls_v += GY.v[m];
+        ls_e += GY.e[m]; ls_u += GY.u[m]; ls_v += GY.v[m]; ls_h += GY.h[m];
     }
+    // the predicted depth h* = eta* - z (the fix is the identity when wet)
+    ls_e += ls_h;
+    ggz[k] -= ls_h;
     const Cell<T> c = cell_at(qn.e, qn.u, qn.v, z, k);
     if (!(c.e - c.z > G.h_dry)) atomicOr(dry, 1u);
     const bool gx = !(i + SX >= 0 && i + SX < G.nx), gy = !(j + SY >= 0 && j + SY < G.ny);
@@ -213,36 +241,40 @@ __global__ void __launch_bounds__(256) k_adj_pred(GridK<T> G, StepK<T> S, const 
     const Cell<T> yn = gy ? ghost(c, sidey, G)
                           : cell_at(qn.e, qn.u, qn.v, z, (size_t)((ptrdiff_t)k + (ptrdiff_t)SY * G.pitch));
     const T gn2 = n2 ? n2[k] : G.gn2;
-    Vjp3<T> lc{0, 0, 0}, lx{0, 0, 0}, ly{0, 0, 0}, lb{Bc.e[k], Bc.u[k], Bc.v[k]};
+    Vjp4<T> lc{0, 0, 0, 0}, lx{0, 0, 0, 0}, ly{0, 0, 0, 0};
+    Vjp3<T> lb{Bc.e[k], Bc.u[k], Bc.v[k]};
     T lf[4] = {0, 0, 0, 0}, lg = T(0);
     stage_vjp<SX, SY>(c, xn, yn, c.e, c.u, c.v, gn2, S, G.h_dry, ls_e, ls_u, ls_v, lc, lx, ly, lf, lb, lg);
     faces_vjp<SX, SY>(i, j, G, c, xn, yn, lf, lc, lx, ly);
-    if (gx) { ghost_vjp(c, sidex, G, lx, lc); lx = Vjp3<T>{0, 0, 0}; }
-    if (gy) { ghost_vjp(c, sidey, G, ly, lc); ly = Vjp3<T>{0, 0, 0}; }
-    Pc.e[k] = lc.e + lb.e; Pc.u[k] = lc.u + lb.u; Pc.v[k] = lc.v + lb.v;
-    PX.e[k] = lx.e; PX.u[k] = lx.u; PX.v[k] = lx.v;
-    PY.e[k] = ly.e; PY.u[k] = ly.u; PY.v[k] = ly.v;
+    if (gx) { ghost_vjp(c, sidex, G, lx, lc); lx = Vjp4<T>{0, 0, 0, 0}; }
+    if (gy) { ghost_vjp(c, sidey, G, ly, lc); ly = Vjp4<T>{0, 0, 0, 0}; }
+    lc.e += lb.e; lc.u += lb.u; lc.v += lb.v;
+    put4(Pc, k, lc);
+    put4(PX, k, lx);
+    put4(PY, k, ly);
     ggn2[k] += lg;
 }
 
 // Step 4: the cotangent of q^n: the cell's own part and the parts its
 // downwind predictor neighbours computed for it.
 template <class T, int SX, int SY>
-__global__ void __launch_bounds__(256) k_adj_gather(GridK<T> G, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY,
-                                                    Planes3<T> lam) {
+__global__ void __launch_bounds__(256) k_adj_gather(GridK<T> G, Planes4<T> Pc, Planes4<T> PX, Planes4<T> PY,
+                                                    Planes3<T> lam, T* __restrict__ ggz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const size_t k = (size_t)j * G.pitch + i;
-    T e = Pc.e[k], u = Pc.u[k], v = Pc.v[k];
+    T e = Pc.e[k], u = Pc.u[k], v = Pc.v[k], h = Pc.h[k];
     if (i - SX >= 0 && i - SX < G.nx) {
         const size_t m = (size_t)((ptrdiff_t)k - SX);
-        e += PX.e[m]; u += PX.u[m]; v += PX.v[m];
+        e += PX.e[m]; u += PX.u[m]; v += PX.v[m]; h += PX.h[m];
     }
     if (j - SY >= 0 && j - SY < G.ny) {
         const size_t m = (size_t)((ptrdiff_t)k - (ptrdiff_t)SY * G.pitch);
-        e += PY.e[m]; u += PY.u[m]; v += PY.v[m];
+        e += PY.e[m]; u += PY.u[m]; v += PY.v[m]; h += PY.h[m];
     }
-    lam.e[k] = e; lam.u[k] = u; lam.v[k] = v;
+    // level n's depth h = eta - z
+    lam.e[k] = e + h; lam.u[k] = u; lam.v[k] = v;
+    ggz[k] -= h;
 }
 
 // Gauge values of a level into out[g]; residuals into lambda_eta at gauges.
@@ -345,8 +377,9 @@ void plain_step_raw(const swe_ctx* c, const GridK<T>& G, DevCtl* ctl, const doub
 }
 
 template <class T, int SX, int SY>
-void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, const double* dtp, Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX, Planes3<T> GY,
-                  Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2, unsigned* dry) {
+void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, const double* dtp, Planes3<T> qn,
+                  Planes3<T> qs, Planes3<T> lam, Planes4<T> Sc, Planes4<T> GX, Planes4<T> GY, Planes3<T> Bc,
+                  Planes4<T> Pc, Planes4<T> PX, Planes4<T> PY, T* ggn2, T* ggz, unsigned* dry) {
     const swe_params& p = c->p;
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const StepK<T> S = make_stepk<T>(dt, p.dx, p.dy, p.g);
@@ -357,8 +390,8 @@ void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, c
     k_adj_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, S, (const T*)c->z, (const T*)c->n2, qn, qs, lam, Sc, GX,
                                                       GY, Bc, ggn2, dry);
     k_adj_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, S, (const T*)c->z, (const T*)c->n2, qn, Sc, GX, GY, Bc, Pc,
-                                                      PX, PY, ggn2, dry);
-    k_adj_gather<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, Pc, PX, PY, lam);
+                                                      PX, PY, ggn2, ggz, dry);
+    k_adj_gather<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, Pc, PX, PY, lam, ggz);
 }
 
 template <class T>
@@ -374,12 +407,13 @@ void dispatch_plain(const swe_ctx* c, const GridK<T>& G, long long k, DevCtl* ct
 
 template <class T>
 void dispatch_adj(const swe_ctx* c, const GridK<T>& G, long long k, double dt, DevCtl* ctl, const double* dtp,
-                  Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes3<T> Sc, Planes3<T> GX,
-                  Planes3<T> GY, Planes3<T> Bc, Planes3<T> Pc, Planes3<T> PX, Planes3<T> PY, T* ggn2,
+                  Planes3<T> qn, Planes3<T> qs, Planes3<T> lam, Planes4<T> Sc, Planes4<T> GX,
+                  Planes4<T> GY, Planes3<T> Bc, Planes4<T> Pc, Planes4<T> PX, Planes4<T> PY, T* ggn2, T* ggz,
                   unsigned* dry) {
     int sx, sy;
     step_dirs(c->p.dir_cycle, k, &sx, &sy);
-#define SWE_ADJ(A_, B_) adj_step_raw<T, A_, B_>(c, G, dt, ctl, dtp, qn, qs, lam, Sc, GX, GY, Bc, Pc, PX, PY, ggn2, dry)
+#define SWE_ADJ(A_, B_) \
+    adj_step_raw<T, A_, B_>(c, G, dt, ctl, dtp, qn, qs, lam, Sc, GX, GY, Bc, Pc, PX, PY, ggn2, ggz, dry)
     if (sx > 0 && sy > 0) SWE_ADJ(1, 1);
     else if (sx > 0) SWE_ADJ(1, -1);
     else if (sy > 0) SWE_ADJ(-1, 1);
@@ -433,7 +467,7 @@ struct SegGraph {
 
 template <class T>
 swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const double* obs, int kcp, double* loss,
-                     double* grad_n, double* grad_eta0) {
+                     double* grad_n, double* grad_eta0, double* grad_z) {
     const swe_params& p = c->p;
     const size_t plane = c->plane, n = (size_t)p.nx * p.ny;
     const GridK<T> G = grid_k<T>(c);
@@ -449,11 +483,20 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
     std::vector<Planes3<T>> cp(nseg > 0 ? nseg : 1), seg(K + 1);
     for (auto& q : cp) ACK(planes(q));
     for (auto& q : seg) ACK(planes(q));
-    Planes3<T> qs, lam, Sc, GX, GY, Bc, Pc, PX, PY;
-    Planes3<T>* all[9] = {&qs, &lam, &Sc, &GX, &GY, &Bc, &Pc, &PX, &PY};
-    for (int q = 0; q < 9; ++q) ACK(planes(*all[q]));
-    T* ggn2 = nullptr;
+    Planes3<T> qs, lam, Bc;
+    Planes3<T>* all3[3] = {&qs, &lam, &Bc};
+    for (int q = 0; q < 3; ++q) ACK(planes(*all3[q]));
+    Planes4<T> Sc, GX, GY, Pc, PX, PY;
+    Planes4<T>* all4[6] = {&Sc, &GX, &GY, &Pc, &PX, &PY};
+    for (int q = 0; q < 6; ++q) {
+        Planes3<T> t3;
+        ACK(planes(t3));
+        all4[q]->e = t3.e; all4[q]->u = t3.u; all4[q]->v = t3.v;
+        ACK(buf.get(&all4[q]->h, plane * sizeof(T)));
+    }
+    T *ggn2 = nullptr, *ggz = nullptr;
     ACK(buf.get(&ggn2, plane * sizeof(T)));
+    ACK(buf.get(&ggz, plane * sizeof(T)));
     long long* gd = nullptr;
     double *gv = nullptr, *res = nullptr, *dtd = nullptr;
     DevCtl* ctl = nullptr;
@@ -537,8 +580,8 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
 
     // ---- reverse
     const int zb = 1024;
-    T* zq[4] = {lam.e, lam.u, lam.v, ggn2};
-    for (int q = 0; q < 4; ++q) k_zero<T><<<zb, 256, 0, c->stream>>>(zq[q], plane);
+    T* zq[5] = {lam.e, lam.u, lam.v, ggn2, ggz};
+    for (int q = 0; q < 5; ++q) k_zero<T><<<zb, 256, 0, c->stream>>>(zq[q], plane);
     if (T_ > 0 && ng > 0) k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(T_ - 1) * ng);
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int s0 = sg * K, s1 = (s0 + K < T_) ? s0 + K : T_;
@@ -551,7 +594,7 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
                 dispatch_plain<T>(c, G, step0 + s, ctl, dtd + s, seg[s - s0], qs, seg[s - s0 + 1]);
             for (int s = s1 - 1; s >= s0; --s) {
                 dispatch_adj<T>(c, G, step0 + s, dts[s], ctl, dtd + s, seg[s - s0], qs, lam, Sc, GX, GY, Bc, Pc, PX,
-                                PY, ggn2, dry);
+                                PY, ggn2, ggz, dry);
                 if (s >= 1 && ng > 0)
                     k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(s - 1) * ng);
             }
@@ -564,22 +607,24 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
             ACK(rgraph.run(enqueue));
         }
     }
-    // ---- outputs: d/d eta0, and d/dn = d/d(g n^2) * 2 g n
+    // ---- outputs: d/d eta0, d/dz, and d/dn = d/d(g n^2) * 2 g n
     unsigned hdry = 0;
     ACK(cudaMemcpyAsync(&hdry, dry, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     ACK(cudaStreamSynchronize(c->stream));
     if (hdry)
         return afail(c, SWE_ERR_UNSUPPORTED,
                      "a cell was at or below the wet threshold during the run: the adjoint covers the fully wet regime");
-    std::vector<T> hb(plane), hg(plane), hn(plane);
+    std::vector<T> hb(plane), hg(plane), hn(plane), hz(grad_z ? plane : 1);
     ACK(cudaMemcpyAsync(hb.data(), lam.e, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
     ACK(cudaMemcpyAsync(hg.data(), ggn2, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    if (grad_z) ACK(cudaMemcpyAsync(hz.data(), ggz, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
     if (c->n2) ACK(cudaMemcpyAsync(hn.data(), c->n2, plane * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
     ACK(cudaStreamSynchronize(c->stream));
     for (int j = 0; j < p.ny; ++j)
         for (int i = 0; i < p.nx; ++i) {
             const size_t k = (size_t)j * c->pitch + i, o = (size_t)j * p.nx + i;
             if (grad_eta0) grad_eta0[o] = (double)hb[k];
+            if (grad_z) grad_z[o] = (double)hz[k];
             if (grad_n) {
                 const double gn2 = c->n2 ? (double)hn[k] : p.g * p.manning_n * p.manning_n;
                 grad_n[o] = (double)hg[k] * 2.0 * std::sqrt(p.g * gn2);
@@ -593,7 +638,7 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
 
 extern "C" swe_status swe_adjoint(swe_ctx* c, int32_t nsteps, const int64_t* gauges, int32_t ngauges,
                                   const double* obs, int32_t checkpoint_every, double* loss, double* grad_n,
-                                  double* grad_eta0) {
+                                  double* grad_eta0, double* grad_z) {
     if (!c) return SWE_ERR_ARG;
     if (c->poisoned) return afail(c, SWE_ERR_STATE, "context poisoned by an earlier CUDA error");
     if (cudaSetDevice(c->p.device) != cudaSuccess) return afail(c, SWE_ERR_CUDA, "cudaSetDevice failed");
@@ -606,6 +651,7 @@ extern "C" swe_status swe_adjoint(swe_ctx* c, int32_t nsteps, const int64_t* gau
     const long long ncell = (long long)c->p.nx * c->p.ny;
     for (int g = 0; g < ngauges; ++g)
         if (gauges[g] < 0 || gauges[g] >= ncell) return afail(c, SWE_ERR_ARG, "gauge %d out of range", g);
-    if (c->real_size == 8) return adjoint_t<double>(c, nsteps, gauges, ngauges, obs, checkpoint_every, loss, grad_n, grad_eta0);
-    return adjoint_t<float>(c, nsteps, gauges, ngauges, obs, checkpoint_every, loss, grad_n, grad_eta0);
+    if (c->real_size == 8)
+        return adjoint_t<double>(c, nsteps, gauges, ngauges, obs, checkpoint_every, loss, grad_n, grad_eta0, grad_z);
+    return adjoint_t<float>(c, nsteps, gauges, ngauges, obs, checkpoint_every, loss, grad_n, grad_eta0, grad_z);
 }

@@ -25,6 +25,7 @@ SWE_ERR_NEGDEPTH, SWE_ERR_TIMEOUT, SWE_ERR_STATE, SWE_ERR_UNSUPPORTED = 4, 5, 6,
 SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_OUTFLOW = 0, 1, 2
 SWE_FP64, SWE_FP32 = 0, 1
 SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN, SWE_KERNEL_PAPER, SWE_KERNEL_PAPER_DEVDT = 0, 1, 2, 3
+SWE_KERNEL_PAPER_SHARED, SWE_KERNEL_PAPER_SHARED_DEVDT = 4, 5
 SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED = 1, 2, 4
 SWE_NOALLOC_MAX_CELLS = 1 << 20
 
@@ -92,7 +93,7 @@ _SIGS = {
     "swe_batch_destroy": (None, [_vp]),
     "swe_batch_last_error": (ctypes.c_char_p, [_vp]),
     "swe_adjoint": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _dp,
-                                   ctypes.c_int32, _dp, _dp, _dp]),
+                                   ctypes.c_int32, _dp, _dp, _dp, _dp]),
     "swe_set_own_rows": (ctypes.c_int, [_ctxp, ctypes.c_int32, ctypes.c_int32]),
     "swe_copy_rows": (ctypes.c_int, [_ctxp, ctypes.c_int32, _ctxp, ctypes.c_int32, ctypes.c_int32]),
     "swe_cfl_combine": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]),
@@ -264,16 +265,21 @@ class Solver:
         _check(self.lib.swe_get_info(self.ctx, ctypes.byref(i)), self.ctx)
         return _info(i)
 
-    def adjoint(self, nsteps: int, gauges, obs, checkpoint_every: int = 0):
+    def adjoint(self, nsteps: int, gauges, obs, checkpoint_every: int = 0, with_bed: bool = False):
         """Loss and its gradient w.r.t. the Manning field and the initial
-        elevation over nsteps steps from the current state (advances it)."""
+        elevation (and, with_bed, the bed elevation) over nsteps steps from
+        the current state (advances it).  Returns (loss, dL/dn, dL/deta0) or
+        (loss, dL/dn, dL/deta0, dL/dz)."""
         g = np.ascontiguousarray(gauges, dtype=np.int64)
         ob = np.ascontiguousarray(obs, dtype=np.float64).reshape(int(nsteps), g.shape[0])
         loss = np.zeros(1)
         gn, ge = np.zeros(self.shape), np.zeros(self.shape)
+        gz = np.zeros(self.shape) if with_bed else None
         st = self.lib.swe_adjoint(self.ctx, int(nsteps), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                  int(g.shape[0]), _p(ob), int(checkpoint_every), _p(loss), _p(gn), _p(ge))
+                                  int(g.shape[0]), _p(ob), int(checkpoint_every), _p(loss), _p(gn), _p(ge), _p(gz))
         _check(st, self.ctx)
+        if with_bed:
+            return float(loss[0]), gn, ge, gz
         return float(loss[0]), gn, ge
 
     def set_own_rows(self, lo: int, hi: int):
