@@ -52,7 +52,7 @@ bool params_ok(const swe_params* p, char* why, size_t n) {
     }
     if (p->precision != SWE_FP64 && p->precision != SWE_FP32) { snprintf(why, n, "bad precision"); return false; }
     if (p->dir_cycle < 0 || p->dir_cycle > 7) { snprintf(why, n, "dir_cycle must lie in [0, 7]"); return false; }
-    if (p->kernel < SWE_KERNEL_FUSED || p->kernel > SWE_KERNEL_PAPER_DEVDT) { snprintf(why, n, "bad kernel"); return false; }
+    if (p->kernel < SWE_KERNEL_FUSED || p->kernel > SWE_KERNEL_PAPER_SHARED_DEVDT) { snprintf(why, n, "bad kernel"); return false; }
     if (p->seg_rows < 0 || p->seg_rows > 4096 || p->cta_warps < 0 || p->cta_warps > 16) {
         snprintf(why, n, "bad seg_rows / cta_warps"); return false;
     }

@@ -7,6 +7,10 @@
 // kernels but reduces the CFL speed on the GPU in the last sub-step, as the
 // fused and plain steps do.
 //
+// SWE_KERNEL_PAPER_SHARED (and its _DEVDT form) is the paper's second design
+// (Sec. 3.2): the sub-steps that read neighbours run in 16 x 16 blocks with
+// the cells and their halo staged in shared memory.
+//
 // It exists to measure the paper's design next to the fused sweep on the
 // same GPU.  The per-cell arithmetic is swe_cell.cuh's, split at the
 // sub-step boundaries, so with the same step sizes its results equal the
@@ -278,6 +282,144 @@ __global__ void __launch_bounds__(BX) k_final(GridK<T> G, const double* __restri
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->flags, (unsigned)SWE_FLAG_NONFINITE);
 }
 
+// ---------------------------------------------------------------- 16x16 shared-memory form
+// The paper's second design (Sec. 3.2): two-dimensional blocks of 16 by 16
+// threads; each thread copies its cell into shared memory, the threads at the
+// block's edges also copy the halo cells, and the sub-steps that read
+// neighbours (S5/S11 continuity, S7/S13 momentum, S15 dissipation) take them
+// from shared memory.  The per-cell sub-steps read no neighbour and keep their
+// row blocks.  The arithmetic is the same per-cell functions, so the results
+// equal the other layouts' bit for bit.
+constexpr int SB = 16;
+
+// Level value at (x, y) or, just outside the grid, the ghost cell there (the
+// one the neighbour reads of nbr() return); zeros farther out (never read).
+template <class T>
+__device__ __forceinline__ Cell<T> cell_or_ghost(const GridK<T>& G, const T* e, const T* u, const T* v, const T* z,
+                                                 const Ghosts<T>& g, int x, int y) {
+    if (x >= 0 && x < G.nx && y >= 0 && y < G.ny) return at(e, u, v, z, (size_t)y * G.pitch + x);
+    if (y >= 0 && y < G.ny) {
+        if (x == -1) return g.side[SIDE_W][y];
+        if (x == G.nx) return g.side[SIDE_E][y];
+    }
+    if (x >= 0 && x < G.nx) {
+        if (y == -1) return g.side[SIDE_S][x];
+        if (y == G.ny) return g.side[SIDE_N][x];
+    }
+    Cell<T> c;
+    c.e = c.u = c.v = c.z = T(0);
+    return c;
+}
+
+// S5 / S11 with the block's cell fluxes and one halo column/row (on the DX /
+// DY side) in shared memory.
+template <class T, int DX, int DY>
+__global__ void __launch_bounds__(SB * SB) k_continuity_sh(GridK<T> G, const double* __restrict__ dtp, double dx,
+                                                           double dy, double g, const T* __restrict__ e0,
+                                                           const T* __restrict__ qx, const T* __restrict__ qy,
+                                                           Ghosts<T> gh, T* __restrict__ eo) {
+    __shared__ T sx[SB][SB + 1];  // column c is grid column i0 + c + XL
+    __shared__ T sy[SB + 1][SB];  // row r is grid row j0 + r + YL
+    constexpr int XL = DX > 0 ? 0 : -1, YL = DY > 0 ? 0 : -1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * SB, j0 = blockIdx.y * SB;
+    const int i = i0 + tx, j = j0 + ty;
+    auto qxat = [&](int x, int y) -> T {  // the flux a face of column x sees (ghost flux just outside)
+        if (y < 0 || y >= G.ny) return T(0);
+        if (x >= 0 && x < G.nx) return qx[(size_t)y * G.pitch + x];
+        if (x == -1 || x == G.nx) { const Cell<T> q = gh.side[x < 0 ? SIDE_W : SIDE_E][y]; return (q.e - q.z) * q.u; }
+        return T(0);
+    };
+    auto qyat = [&](int x, int y) -> T {
+        if (x < 0 || x >= G.nx) return T(0);
+        if (y >= 0 && y < G.ny) return qy[(size_t)y * G.pitch + x];
+        if (y == -1 || y == G.ny) { const Cell<T> q = gh.side[y < 0 ? SIDE_S : SIDE_N][x]; return (q.e - q.z) * q.v; }
+        return T(0);
+    };
+    sx[ty][tx - XL] = qxat(i, j);
+    sy[ty - YL][tx] = qyat(i, j);
+    if (tx == 0) sx[ty][DX > 0 ? SB : 0] = qxat(i0 + (DX > 0 ? SB : -1), j);
+    if (ty == 0) sy[DY > 0 ? SB : 0][tx] = qyat(i, j0 + (DY > 0 ? SB : -1));
+    __syncthreads();
+    if (i >= G.nx || j >= G.ny) return;
+    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const size_t k = (size_t)j * G.pitch + i;
+    const T qxc = sx[ty][tx - XL], qxn = sx[ty][tx - XL + DX];
+    const T qyc = sy[ty - YL][tx], qyn = sy[ty - YL + DY][tx];
+    T fe, fw, fn, fs;
+    faces<DX>(qxc, qxn, i == 0, i == G.nx - 1, SIDE_W, SIDE_E, G, fe, fw);
+    faces<DY>(qyc, qyn, j == 0, j == G.ny - 1, SIDE_S, SIDE_N, G, fn, fs);
+    eo[k] = continuity(e0[k], fe, fw, fn, fs, S);
+}
+
+// S7 / S13 with the block's cells and one halo column/row in shared memory.
+template <class T, int DX, int DY>
+__global__ void __launch_bounds__(SB * SB) k_momentum_sh(GridK<T> G, const double* __restrict__ dtp, double dx,
+                                                         double dy, double g, const T* __restrict__ e,
+                                                         const T* __restrict__ u, const T* __restrict__ v,
+                                                         const T* __restrict__ z, Ghosts<T> gh,
+                                                         const T* __restrict__ C, const T* __restrict__ u0,
+                                                         const T* __restrict__ v0, T* __restrict__ uo,
+                                                         T* __restrict__ vo) {
+    __shared__ Cell<T> sc[SB][SB];
+    __shared__ Cell<T> hx[SB];  // the column past the block on the DX side
+    __shared__ Cell<T> hy[SB];  // the row past the block on the DY side
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * SB, j0 = blockIdx.y * SB;
+    const int i = i0 + tx, j = j0 + ty;
+    sc[ty][tx] = cell_or_ghost(G, e, u, v, z, gh, i, j);
+    if (tx == 0) hx[ty] = cell_or_ghost(G, e, u, v, z, gh, i0 + (DX > 0 ? SB : -1), j);
+    if (ty == 0) hy[tx] = cell_or_ghost(G, e, u, v, z, gh, i, j0 + (DY > 0 ? SB : -1));
+    __syncthreads();
+    if (i >= G.nx || j >= G.ny) return;
+    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const size_t k = (size_t)j * G.pitch + i;
+    const int txn = tx + DX, tyn = ty + DY;
+    const Cell<T> xn = (txn >= 0 && txn < SB) ? sc[ty][txn] : hx[ty];
+    const Cell<T> yn = (tyn >= 0 && tyn < SB) ? sc[tyn][tx] : hy[tx];
+    T a, b;
+    momentum<DX, DY>(sc[ty][tx], xn, yn, C[k], u0[k], v0[k], S, G.h_dry, a, b);
+    uo[k] = a;
+    vo[k] = b;
+}
+
+// S15 with the block's depths (halo 2) and e, u, v (halo 1) in shared
+// memory, each at the clamped grid position the global form reads.
+template <class T>
+__global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const T* __restrict__ e,
+                                                            const T* __restrict__ u, const T* __restrict__ v,
+                                                            const T* __restrict__ z, T* __restrict__ e1,
+                                                            T* __restrict__ u1, T* __restrict__ v1) {
+    __shared__ T sh[SB + 4][SB + 4];
+    __shared__ T sf[3][SB + 2][SB + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * SB + tx;
+    const int i0 = blockIdx.x * SB, j0 = blockIdx.y * SB;
+    auto clampx = [&](int x) { return x < 0 ? 0 : (x >= G.nx ? G.nx - 1 : x); };
+    auto clampy = [&](int y) { return y < 0 ? 0 : (y >= G.ny ? G.ny - 1 : y); };
+    for (int q = t; q < (SB + 4) * (SB + 4); q += SB * SB) {
+        const int r = q / (SB + 4), c = q % (SB + 4);
+        const size_t k = (size_t)clampy(j0 + r - 2) * G.pitch + clampx(i0 + c - 2);
+        sh[r][c] = e[k] - z[k];
+    }
+    for (int q = t; q < (SB + 2) * (SB + 2); q += SB * SB) {
+        const int r = q / (SB + 2), c = q % (SB + 2);
+        const size_t k = (size_t)clampy(j0 + r - 1) * G.pitch + clampx(i0 + c - 1);
+        sf[0][r][c] = e[k];
+        sf[1][r][c] = u[k];
+        sf[2][r][c] = v[k];
+    }
+    __syncthreads();
+    const int i = i0 + tx, j = j0 + ty;
+    if (i >= G.nx || j >= G.ny) return;
+    const size_t k = (size_t)j * G.pitch + i;
+    auto hat = [&](int ii, int jj) -> T { return sh[jj - j0 + 2][ii - i0 + 2]; };
+    auto atf = [&](int f, int ii, int jj) -> T { return sf[f][jj - j0 + 1][ii - i0 + 1]; };
+    T a = e1[k], b = u1[k], d = v1[k];
+    dissipation_core(G, i, j, hat, atf, sf[0][ty + 1][tx + 1], sf[1][ty + 1][tx + 1], sf[2][ty + 1][tx + 1], z[k], a,
+                     b, d);
+    e1[k] = a; u1[k] = b; v1[k] = d;
+}
+
 template <class T>
 void free_scratch(Scratch<T>* q) {
     T* dev[] = {q->h, q->qx, q->qy, q->C, q->es, q->us, q->vs, q->qxs, q->qys, q->Cs, q->ec, q->uc, q->vc};
@@ -372,7 +514,9 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
     cudaError_t err;
     // S2: the step size
     const bool fixed = c->dt_fixed_cap > 0 && c->dt_fixed;
-    const bool devdt = p.kernel == SWE_KERNEL_PAPER_DEVDT;
+    const bool devdt = p.kernel == SWE_KERNEL_PAPER_DEVDT || p.kernel == SWE_KERNEL_PAPER_SHARED_DEVDT;
+    const bool shared = p.kernel == SWE_KERNEL_PAPER_SHARED || p.kernel == SWE_KERNEL_PAPER_SHARED_DEVDT;
+    const dim3 sblk(SB, SB), sgrd((p.nx + SB - 1) / SB, (p.ny + SB - 1) / SB);
     const double* dtv = fixed ? c->dt_fixed + s : q->d_dt;
     if (!fixed && !devdt) {
         double dt = 0.0;
@@ -389,20 +533,38 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
     k_s1<T><<<grd, blk, 0, c->stream>>>(G, e, z, q->h, q->wet);                                           // S1
     k_ghosts<T><<<gb, 256, 0, c->stream>>>(G, e, u, v, z, q->gn);                                          // S3
     k_fluxes<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, q->qx, q->qy);                                  // S4
-    k_continuity<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qx, q->qy, q->gn, q->es);  // S5
+    if (shared)
+        k_continuity_sh<T, SX, SY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qx, q->qy, q->gn, q->es);
+    else
+        k_continuity<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qx, q->qy, q->gn, q->es);  // S5
     k_friction<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, n2, q->C);                                    // S6
-    k_momentum<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, q->gn, q->C, u, v, q->us,
-                                                      q->vs);                                              // S7
+    if (shared)
+        k_momentum_sh<T, SX, SY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, q->gn, q->C, u, v,
+                                                               q->us, q->vs);
+    else
+        k_momentum<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, q->gn, q->C, u, v, q->us,
+                                                          q->vs);                                          // S7
     k_fix_pred<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, c->ctl, area);                    // S8
     k_ghosts<T><<<gb, 256, 0, c->stream>>>(G, q->es, q->us, q->vs, z, q->gs);                              // S9
     k_fluxes<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, q->qxs, q->qys);                    // S10
-    k_continuity<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qxs, q->qys, q->gs,
-                                                        q->ec);                                            // S11
+    if (shared)
+        k_continuity_sh<T, CX, CY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qxs, q->qys, q->gs,
+                                                                 q->ec);
+    else
+        k_continuity<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qxs, q->qys, q->gs,
+                                                            q->ec);                                        // S11
     k_friction<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, n2, q->Cs);                       // S12
-    k_momentum<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, q->es, q->us, q->vs, z, q->gs, q->Cs,
-                                                      u, v, q->uc, q->vc);                                 // S13
+    if (shared)
+        k_momentum_sh<T, CX, CY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, q->es, q->us, q->vs, z, q->gs,
+                                                               q->Cs, u, v, q->uc, q->vc);
+    else
+        k_momentum<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, q->es, q->us, q->vs, z, q->gs,
+                                                          q->Cs, u, v, q->uc, q->vc);                      // S13
     k_average<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, q->ec, q->uc, q->vc, e1, u1, v1);     // S14
-    if (p.kappa != 0.0) k_dissipation<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, e1, u1, v1);           // S15
+    if (p.kappa != 0.0) {                                                                                  // S15
+        if (shared) k_dissipation_sh<T><<<sgrd, sblk, 0, c->stream>>>(G, e, u, v, z, e1, u1, v1);
+        else k_dissipation<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, e1, u1, v1);
+    }
     k_final<T><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, e, u, v, z, q->qxs, q->qys, e1, u1, v1, c->ctl,
                                            devdt ? 1 : 0, slot_next, area);                                // S16
     return cudaGetLastError();

@@ -47,6 +47,29 @@ static __global__ void k_plain_dt(DevCtl* ctl, int slot, int slot_next, const do
 // the cell's own values e0, u0, v0, zc) added to the averaged en, un, vn.
 // Neighbour depths outside the grid repeat the edge cell; faces on the
 // boundary carry none.
+// The arithmetic, given accessors of the neighbours' depth hat(ii, jj) and of
+// field f (0: e, 1: u, 2: v) at(f, ii, jj), both at the clamped position.
+template <class T, class HAT, class AT>
+__device__ __forceinline__ void dissipation_core(const GridK<T>& G, int i, int j, HAT&& hat, AT&& at, T e0, T u0,
+                                                 T v0, T zc, T& en, T& un, T& vn) {
+    const T hc = e0 - zc;
+    const T hxm2 = hat(i - 2, j), hxm1 = hat(i - 1, j), hxp1 = hat(i + 1, j), hxp2 = hat(i + 2, j);
+    const T hym2 = hat(i, j - 2), hym1 = hat(i, j - 1), hyp1 = hat(i, j + 1), hyp2 = hat(i, j + 2);
+    const T hd = G.h_dry;
+    const bool wc = hc > hd;
+    const T nxc = nu_switch(hxm1, hc, hxp1), nyc = nu_switch(hym1, hc, hyp1);
+    T ee = (i + 1 < G.nx) ? face_eps(wc, hxp1 > hd, nxc, nu_switch(hc, hxp1, hxp2)) : T(0);
+    T ew = (i - 1 >= 0) ? face_eps(hxm1 > hd, wc, nu_switch(hxm2, hxm1, hc), nxc) : T(0);
+    T en2 = (j + 1 < G.ny) ? face_eps(wc, hyp1 > hd, nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
+    T es2 = (j - 1 >= 0) ? face_eps(hym1 > hd, wc, nu_switch(hym2, hym1, hc), nyc) : T(0);
+    en = dissip_faces(en, dflux(ee, at(0, i + 1, j), e0), dflux(ew, e0, at(0, i - 1, j)),
+                      dflux(en2, at(0, i, j + 1), e0), dflux(es2, e0, at(0, i, j - 1)), G.kappa);
+    un = dissip_faces(un, dflux(ee, at(1, i + 1, j), u0), dflux(ew, u0, at(1, i - 1, j)),
+                      dflux(en2, at(1, i, j + 1), u0), dflux(es2, u0, at(1, i, j - 1)), G.kappa);
+    vn = dissip_faces(vn, dflux(ee, at(2, i + 1, j), v0), dflux(ew, v0, at(2, i - 1, j)),
+                      dflux(en2, at(2, i, j + 1), v0), dflux(es2, v0, at(2, i, j - 1)), G.kappa);
+}
+
 template <class T>
 __device__ __forceinline__ void dissipation_at(const GridK<T>& G, int i, int j, const T* __restrict__ e,
                                                const T* __restrict__ u, const T* __restrict__ v,
@@ -58,27 +81,13 @@ __device__ __forceinline__ void dissipation_at(const GridK<T>& G, int i, int j, 
         size_t q = (size_t)jj * G.pitch + ii;
         return e[q] - z[q];
     };
-    auto at = [&](const T* f, int ii, int jj) -> T {
+    auto at = [&](int f, int ii, int jj) -> T {
         ii = ii < 0 ? 0 : (ii >= G.nx ? G.nx - 1 : ii);
         jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
-        return f[(size_t)jj * G.pitch + ii];
+        const T* p = f == 0 ? e : (f == 1 ? u : v);
+        return p[(size_t)jj * G.pitch + ii];
     };
-    const T hc = e0 - zc;
-    const T hxm2 = hat(i - 2, j), hxm1 = hat(i - 1, j), hxp1 = hat(i + 1, j), hxp2 = hat(i + 2, j);
-    const T hym2 = hat(i, j - 2), hym1 = hat(i, j - 1), hyp1 = hat(i, j + 1), hyp2 = hat(i, j + 2);
-    const T hd = G.h_dry;
-    const bool wc = hc > hd;
-    const T nxc = nu_switch(hxm1, hc, hxp1), nyc = nu_switch(hym1, hc, hyp1);
-    T ee = (i + 1 < G.nx) ? face_eps(wc, hxp1 > hd, nxc, nu_switch(hc, hxp1, hxp2)) : T(0);
-    T ew = (i - 1 >= 0) ? face_eps(hxm1 > hd, wc, nu_switch(hxm2, hxm1, hc), nxc) : T(0);
-    T en2 = (j + 1 < G.ny) ? face_eps(wc, hyp1 > hd, nyc, nu_switch(hc, hyp1, hyp2)) : T(0);
-    T es2 = (j - 1 >= 0) ? face_eps(hym1 > hd, wc, nu_switch(hym2, hym1, hc), nyc) : T(0);
-    en = dissip_faces(en, dflux(ee, at(e, i + 1, j), e0), dflux(ew, e0, at(e, i - 1, j)),
-                      dflux(en2, at(e, i, j + 1), e0), dflux(es2, e0, at(e, i, j - 1)), G.kappa);
-    un = dissip_faces(un, dflux(ee, at(u, i + 1, j), u0), dflux(ew, u0, at(u, i - 1, j)),
-                      dflux(en2, at(u, i, j + 1), u0), dflux(es2, u0, at(u, i, j - 1)), G.kappa);
-    vn = dissip_faces(vn, dflux(ee, at(v, i + 1, j), v0), dflux(ew, v0, at(v, i - 1, j)),
-                      dflux(en2, at(v, i, j + 1), v0), dflux(es2, v0, at(v, i, j - 1)), G.kappa);
+    dissipation_core(G, i, j, hat, at, e0, u0, v0, zc, en, un, vn);
 }
 
 template <class T, int SX, int SY>

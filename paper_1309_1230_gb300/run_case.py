@@ -26,7 +26,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--kernel", default="fused", choices=["fused", "plain", "paper", "paper_devdt"])
+    ap.add_argument("--kernel", default="fused",
+                    choices=["fused", "plain", "paper", "paper_devdt", "paper_shared", "paper_shared_devdt"])
     ap.add_argument("--seg-rows", type=int, default=0, help="rows per work item (0: automatic)")
     ap.add_argument("--dry-skip", type=int, default=1, choices=[0, 1], help="skip all-dry work items")
     a = ap.parse_args(argv)
@@ -46,7 +47,8 @@ def main(argv=None):
         case = I.basin_hump(a.n, a.n, manning_n=0.03, kappa=0.25)
     prec = swe.SWE_FP32 if a.precision == "fp32" else swe.SWE_FP64
     kern = {"fused": swe.SWE_KERNEL_FUSED, "plain": swe.SWE_KERNEL_PLAIN, "paper": swe.SWE_KERNEL_PAPER,
-            "paper_devdt": swe.SWE_KERNEL_PAPER_DEVDT}[a.kernel]
+            "paper_devdt": swe.SWE_KERNEL_PAPER_DEVDT, "paper_shared": swe.SWE_KERNEL_PAPER_SHARED,
+            "paper_shared_devdt": swe.SWE_KERNEL_PAPER_SHARED_DEVDT}[a.kernel]
     s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=case["kappa"], bc=case["bc"],
                    q_in=case["q_in"], precision=prec, kernel=kern, seg_rows=a.seg_rows, dry_skip=a.dry_skip)
     s.set_bed(case["z"])

@@ -22,6 +22,9 @@ pytestmark = pytest.mark.gpu
 
 CASES = {
     "dambreak": (lambda: I.dam_break(260, 90, seed=3), 80),
+    # sizes that are not multiples of the 16 x 16 blocks, and thin grids
+    "ragged": (lambda: I.dam_break(37, 23, seed=11), 60),
+    "thin": (lambda: I.river(5, 70, seed=2), 60),
     "river": (lambda: I.river(300, 70, seed=7), 80),
     "basin_k": (lambda: I.basin_hump(64, 64, manning_n=0.03, kappa=0.25), 60),
     "aniso_river": (lambda: I.with_cell_size(I.open_river(150, 70, seed=7), 0.7, 1.9), 60),
@@ -52,9 +55,13 @@ def test_paper_layout_bitwise_with_the_same_step_sizes(name, precision):
     dts, plain, pinfo = _run(case, precision, swe.SWE_KERNEL_PLAIN, steps)
     _, replay, _ = _run(case, precision, swe.SWE_KERNEL_PAPER, steps, dt_fixed=dts)
     ddts, devdt, dinfo = _run(case, precision, swe.SWE_KERNEL_PAPER_DEVDT, steps, calls=2)
-    assert np.array_equal(ddts, dts)
-    for a, b, c in zip(replay, devdt, plain):
+    # the 16 x 16 shared-memory design (Sec. 3.2), with replayed and GPU step sizes
+    _, sreplay, _ = _run(case, precision, swe.SWE_KERNEL_PAPER_SHARED, steps, dt_fixed=dts)
+    sdts, sdevdt, _ = _run(case, precision, swe.SWE_KERNEL_PAPER_SHARED_DEVDT, steps, calls=3)
+    assert np.array_equal(ddts, dts) and np.array_equal(sdts, dts)
+    for a, b, c, d, f in zip(replay, devdt, plain, sreplay, sdevdt):
         assert np.array_equal(a, c) and np.array_equal(b, c)
+        assert np.array_equal(d, c) and np.array_equal(f, c)
     assert dinfo.t == pinfo.t
     # tallies are FP64 sums whose order differs between the layouts
     assert dinfo.clamp_volume == pytest.approx(pinfo.clamp_volume, rel=1e-9, abs=1e-9)
@@ -62,12 +69,14 @@ def test_paper_layout_bitwise_with_the_same_step_sizes(name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_paper_layout_host_step_size(precision):
+@pytest.mark.parametrize("shared", [False, True])
+def test_paper_layout_host_step_size(precision, shared):
     from paper_1309_1230_gb300 import swe
     case = I.dam_break(260, 90, seed=3)
     steps = 60
     dts, plain, _ = _run(case, precision, swe.SWE_KERNEL_PLAIN, steps)
-    hdts, host, info = _run(case, precision, swe.SWE_KERNEL_PAPER, steps, calls=3)
+    kern = swe.SWE_KERNEL_PAPER_SHARED if shared else swe.SWE_KERNEL_PAPER
+    hdts, host, info = _run(case, precision, kern, steps, calls=3)
     assert np.max(np.abs(hdts - dts) / dts) <= (1e-12 if precision == swe.SWE_FP64 else 1e-6)
     emax, _ = rel_depth_err(host[0] - case["z"], plain[0] - case["z"])
     assert emax <= (1e-10 if precision == swe.SWE_FP64 else 1e-4), emax
