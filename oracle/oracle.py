@@ -38,6 +38,7 @@ class _Params(ctypes.Structure):
         ("kappa", ctypes.c_double), ("manning_n", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("q_in", ctypes.c_double * 4),
         ("dir_cycle", ctypes.c_int32),
+        ("friction", ctypes.c_int32), ("dissipation", ctypes.c_int32),
     ]
 
 
@@ -47,7 +48,9 @@ class Params:
 
     q_in is the discharge per unit width entering the domain (m^2/s).
     dir_cycle: bit 0 alternates the predictor directions every step,
-    bit 1 starts x backward, bit 2 starts y backward.
+    bit 1 starts x backward, bit 2 starts y backward.  friction and
+    dissipation select the ablation forms (explicit friction; the
+    TVD-MacCormack term in place of S15's switch).
     """
     nx: int
     ny: int
@@ -62,6 +65,8 @@ class Params:
     bc: tuple = (WALL, WALL, WALL, WALL)
     q_in: tuple = (0.0, 0.0, 0.0, 0.0)
     dir_cycle: int = 1
+    friction: int = 0       # 0: point-implicit Manning; 1: explicit (ablation)
+    dissipation: int = 0    # 0: the switch form of S15 (kappa); 1: the TVD-MacCormack term
 
     def _c(self) -> _Params:
         p = _Params()
@@ -72,6 +77,7 @@ class Params:
             p.bc[s] = int(self.bc[s])
             p.q_in[s] = float(self.q_in[s])
         p.dir_cycle = int(self.dir_cycle)
+        p.friction, p.dissipation = int(self.friction), int(self.dissipation)
         return p
 
 

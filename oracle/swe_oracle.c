@@ -65,6 +65,8 @@ typedef struct {
     int32_t bc[4];      /* W, E, S, N: BC_WALL / BC_INFLOW / BC_OUTFLOW */
     double q_in[4];     /* inflow discharge per unit width INTO the domain, m^2/s */
     int32_t dir_cycle;  /* predictor direction schedule, see step_dirs() */
+    int32_t friction;   /* 0: point-implicit Manning (the reading used throughout); 1: explicit */
+    int32_t dissipation;/* 0: S15 as below (kappa); 1: the TVD-MacCormack term (kappa ignored) */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -262,7 +264,9 @@ static void friction(const orc_params* p, work* w, const double* h, const unsign
 
 /* S7 / S13: momentum.  The differenced state (eta, u, v, wet) is the
  * predictor input for S7 and the predicted state for S13; u_n, v_n are
- * always the level-n velocities.  out = (vel_n - dt*A) / (1 + dt*C). */
+ * always the level-n velocities.  out = (vel_n - dt*A) / (1 + dt*C), or with
+ * explicit friction (the ablation) out = vel_n - dt*A - dt*C*vel, C and vel
+ * those of the differenced state. */
 static void momentum(const orc_params* p, work* w, double dt, int sx, int sy,
                      const double* eta, const double* u, const double* v,
                      const unsigned char* wet, const double* C,
@@ -284,9 +288,14 @@ static void momentum(const orc_params* p, work* w, double dt, int sx, int sy,
             else        { duy = u[c] - u[yn]; dvy = v[c] - v[yn]; dey = eta[c] - ey; }
             double Au = u[c] * dux / p->dx + v[c] * duy / p->dy + p->g * dex / p->dx;
             double Av = u[c] * dvx / p->dx + v[c] * dvy / p->dy + p->g * dey / p->dy;
-            double den = 1.0 + dt * C[c];
-            u_out[c] = (u_n[c] - dt * Au) / den;
-            v_out[c] = (v_n[c] - dt * Av) / den;
+            if (p->friction == 1) {
+                u_out[c] = (u_n[c] - dt * Au) - dt * C[c] * u[c];
+                v_out[c] = (v_n[c] - dt * Av) - dt * C[c] * v[c];
+            } else {
+                double den = 1.0 + dt * C[c];
+                u_out[c] = (u_n[c] - dt * Au) / den;
+                v_out[c] = (v_n[c] - dt * Av) / den;
+            }
         }
 }
 
@@ -396,6 +405,69 @@ static void dissipation(const orc_params* p, work* w) {
         }
 }
 
+/* S15, TVD-MacCormack form (the ablation; Davis 1984, applied to shallow
+ * water by Garcia-Navarro, Alcrudo and Saviron 1992).  Per axis and per field
+ * phi of level n, with the face differences D_{i+1/2} = phi_{i+1} - phi_i
+ * (0 for a face outside the grid):
+ *   r+_i = D_{i-1/2} D_{i+1/2} / D_{i+1/2}^2,  r-_i = D_{i-1/2} D_{i+1/2} / D_{i-1/2}^2
+ *          (0 when the denominator is 0),
+ *   psi(r) = max(0, min(2 r, 1)),  C(nu) = nu (1 - nu) for nu <= 1/2, else 1/4,
+ *   nu_i = (|vel_i| + sqrt(g h_i)) dt / dx (0 for a dry cell), G = C(nu) (1 - psi) / 2,
+ * and the face term T_{i+1/2} = (G(nu_i, r+_i) + G(nu_{i+1}, r-_{i+1})) D_{i+1/2}
+ * on interior faces between two wet cells (0 on every other face);
+ * phi += (T_{i+1/2} - T_{i-1/2}) + (the same along y).  In face form it
+ * conserves mass; it vanishes where the differences do (lake at rest). */
+static double tvd_psi(double r) { return fmax(0.0, fmin(2.0 * r, 1.0)); }
+static double tvd_c(double nu) { return nu <= 0.5 ? nu * (1.0 - nu) : 0.25; }
+static double tvd_ratio(double num, double den) { return den != 0.0 ? num / den : 0.0; }
+
+/* T at the face between cells a (low side) and b (high side) along one axis:
+ * dm = D below a's face, d = D of this face, dp = D above b's face. */
+static double tvd_face(double dm, double d, double dp, double nua, double nub) {
+    double rpa = tvd_ratio(dm * d, d * d);   /* r+ of cell a */
+    double rmb = tvd_ratio(d * dp, d * d);   /* r- of cell b: D_{b-1/2} = d, D_{b+1/2} = dp */
+    double ga = 0.5 * tvd_c(nua) * (1.0 - tvd_psi(rpa));
+    double gb = 0.5 * tvd_c(nub) * (1.0 - tvd_psi(rmb));
+    return (ga + gb) * d;
+}
+
+static void tvd_dissipation(const orc_params* p, work* w, double dt) {
+    const int nx = w->nx, ny = w->ny;
+    const double* h = w->h;
+    const double* fld[3] = {w->eta, w->u, w->v};
+    double* out[3] = {w->e1, w->u1, w->v1};
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = G(i, j);
+            w->nux[c] = w->wet[c] ? (fabs(w->u[c]) + sqrt(p->g * h[c])) * dt / p->dx : 0.0;
+            w->nuy[c] = w->wet[c] ? (fabs(w->v[c]) + sqrt(p->g * h[c])) * dt / p->dy : 0.0;
+        }
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = G(i, j);
+            for (int f = 0; f < 3; ++f) {
+                const double* q = fld[f];
+                /* differences of the faces i-3/2 .. i+3/2 (x) and j-3/2 .. j+3/2 (y) */
+                #define DX_(ii) (((ii) >= 0 && (ii) + 1 < nx) ? q[G((ii) + 1, j)] - q[G((ii), j)] : 0.0)
+                #define DY_(jj) (((jj) >= 0 && (jj) + 1 < ny) ? q[G(i, (jj) + 1)] - q[G(i, (jj))] : 0.0)
+                double te = 0.0, tw = 0.0, tn = 0.0, ts = 0.0;
+                if (i + 1 < nx && w->wet[c] && w->wet[G(i + 1, j)])
+                    te = tvd_face(DX_(i - 1), DX_(i), DX_(i + 1), w->nux[c], w->nux[G(i + 1, j)]);
+                if (i - 1 >= 0 && w->wet[c] && w->wet[G(i - 1, j)])
+                    tw = tvd_face(DX_(i - 2), DX_(i - 1), DX_(i), w->nux[G(i - 1, j)], w->nux[c]);
+                if (j + 1 < ny && w->wet[c] && w->wet[G(i, j + 1)])
+                    tn = tvd_face(DY_(j - 1), DY_(j), DY_(j + 1), w->nuy[c], w->nuy[G(i, j + 1)]);
+                if (j - 1 >= 0 && w->wet[c] && w->wet[G(i, j - 1)])
+                    ts = tvd_face(DY_(j - 2), DY_(j - 1), DY_(j), w->nuy[G(i, j - 1)], w->nuy[c]);
+                #undef DX_
+                #undef DY_
+                out[f][c] = out[f][c] + ((te - tw) + (tn - ts));
+            }
+        }
+}
+
 /* One full time step n -> n+1 as the 16 sub-steps, each a full-grid pass.
  * On return w->eta/u/v hold level n+1; tallies accumulate into acc[0..4]. */
 static int one_step(const orc_params* p, work* w, int64_t k, double dt_in, int use_dt_in,
@@ -429,7 +501,8 @@ static int one_step(const orc_params* p, work* w, int64_t k, double dt_in, int u
             w->u1[c] = 0.5 * (w->us[c] + w->uss[c]);
             w->v1[c] = 0.5 * (w->vs[c] + w->vss[c]);
         }
-    if (p->kappa != 0.0) dissipation(p, w);                                   /* S15 */
+    if (p->dissipation == 1) tvd_dissipation(p, w, dt);                       /* S15 */
+    else if (p->kappa != 0.0) dissipation(p, w);
     /* S16: fix of level n+1, boundary and clamp tallies, finiteness */
     wetdry_fix(p, w, w->e1, w->u1, w->v1, w->h, w->wet, w->row_b);
     double clamp_final = sum_rows(w->row_b, ny);
@@ -467,6 +540,7 @@ static int check_params(const orc_params* p) {
     if (!(p->h_dry > 0) || !(p->dt_max > 0) || !(p->kappa >= 0) || !(p->manning_n >= 0)) return 0;
     for (int s = 0; s < 4; ++s) if (p->bc[s] < BC_WALL || p->bc[s] > BC_OUTFLOW) return 0;
     if (p->dir_cycle < 0 || p->dir_cycle > 7) return 0;
+    if (p->friction < 0 || p->friction > 1 || p->dissipation < 0 || p->dissipation > 1) return 0;
     return 1;
 }
 
@@ -863,7 +937,7 @@ int orc_adjoint(const orc_params* p, const double* z, const double* nfield, cons
                 const int64_t* gauges, int32_t ng, const double* obs, double* loss, double* grad_n,
                 double* grad_eta0, double* grad_u0, double* grad_v0, double* grad_z) {
     if (!check_params(p) || !z || !nfield || !eta0 || !u0 || !v0 || !dt || T < 0 || ng < 0 || !loss) return ORC_ERR_ARG;
-    if (p->kappa != 0.0) return ORC_ERR_NOT_WET;
+    if (p->kappa != 0.0 || p->friction != 0 || p->dissipation != 0) return ORC_ERR_NOT_WET;
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny, nc = (size_t)(nx + 2) * (ny + 2);
     for (int32_t g = 0; g < ng; ++g)

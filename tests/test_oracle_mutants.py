@@ -9,6 +9,7 @@ import os
 
 import pytest
 
+from tests import test_oracle_ablations as abl
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -49,6 +50,12 @@ MUTANTS = {
     "volume without cell area": ("return s * p->dx * p->dy;", "return s;"),
     "volume times dx only": ("return s * p->dx * p->dy;", "return s * p->dx;"),
     "clamp tally without cell area": ("const double cell_area = p->dx * p->dy;", "const double cell_area = 1.0;"),
+    # the ablation forms
+    "explicit friction sign": ("(u_n[c] - dt * Au) - dt * C[c] * u[c];", "(u_n[c] - dt * Au) + dt * C[c] * u[c];"),
+    "explicit friction on level-n velocity": ("(u_n[c] - dt * Au) - dt * C[c] * u[c];",
+                                              "(u_n[c] - dt * Au) - dt * C[c] * u_n[c];"),
+    "TVD face term difference of coefficients": ("return (ga + gb) * d;", "return (ga - gb) * d;"),
+    "TVD limiter ratio of the wrong cell": ("double rmb = tvd_ratio(d * dp, d * d);", "double rmb = tvd_ratio(d * dp, dp * dp);"),
 }
 
 PIN_CALLS = [
@@ -71,6 +78,10 @@ PIN_CALLS = [
     (pins.test_seiche_period_matches_sqrt_gh, {}),
     (pins.test_uniform_flow_friction_recursion_and_manning, {}),
     (pins.test_degenerate_grids_run, {}),
+    (abl.test_friction_treatments_converge_to_the_decay_closed_form, {}),
+    (abl.test_tvd_term_keeps_the_dam_break_total_variation, {}),
+    (abl.test_tvd_term_mirror_and_transpose_symmetry, {}),
+    (abl.test_ablations_conserve_mass_and_keep_a_lake_at_rest, dict(friction=1, dissipation=1)),
 ]
 
 

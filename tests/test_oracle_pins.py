@@ -280,7 +280,7 @@ def test_seiche_period_matches_sqrt_gh(oracle):
 
 
 # ---------------------------------------------------------------- dam breaks
-def _dambreak_1d(O, N, h0, h1, T, length=2000.0):
+def _dambreak_1d(O, N, h0, h1, T, length=2000.0, kappa=0.25, dissipation=0):
     dx = length / N
     x = (np.arange(N) + 0.5) * dx
     x0 = length / 2.0
@@ -291,7 +291,7 @@ def _dambreak_1d(O, N, h0, h1, T, length=2000.0):
     dt = 0.3 * dx / (2.0 * c0)
     nsteps = int(round(T / dt))
     dt = T / nsteps
-    p = O.Params(nx=N, ny=1, dx=dx, dy=dx, manning_n=0.0, kappa=0.25)
+    p = O.Params(nx=N, ny=1, dx=dx, dy=dx, manning_n=0.0, kappa=kappa, dissipation=dissipation)
     r = O.run(p, z, eta, zeros, zeros, nsteps, dt_fixed=np.full(nsteps, dt))
     assert r.status == 0
     return x - x0, r.eta[0], r.u[0], dx
