@@ -118,14 +118,23 @@ typedef struct {
     int32_t cta_warps;      /* fused kernel: warps per CTA, 0 = automatic */
     int32_t use_graph;      /* capture multi-step calls in CUDA graphs (default 1) */
     int32_t dry_skip;       /* skip all-dry work items (default 1) */
+    /* Ablation forms (0 = the readings of the header comment, the default).
+     * friction 1: explicit friction, u* = u - dt (A + C u) with C and u of the
+     * stage's differenced state, in place of the point-implicit update.
+     * dissipation 1: the TVD-MacCormack term (Davis; Garcia-Navarro, Alcrudo
+     * and Saviron for shallow water) in place of S15's switch form, kappa
+     * ignored.  Only the plain and paper-layout kernels run them; the fused,
+     * batched, adjoint and no-allocation paths answer SWE_ERR_UNSUPPORTED. */
+    int32_t friction;
+    int32_t dissipation;
     /* reserved[0], reserved[1]: test hooks of the batched step (ignored
      * elsewhere; 0 = off).  reserved[0]: the grid-barrier wait limit in
      * microseconds (default about 2 s, at most 10 s).  reserved[1]: the CTA
      * of index reserved[1] - 1 withholds its arrival at the first grid
      * barrier of the next swe_batch_step call (that call only), so that the
      * other CTAs' bounded waits run out and the call returns
-     * SWE_ERR_TIMEOUT.  reserved[2..3] are unused (keep them 0). */
-    int32_t reserved[4];
+     * SWE_ERR_TIMEOUT. */
+    int32_t reserved[2];
 } swe_params;
 
 typedef struct {

@@ -646,6 +646,8 @@ extern "C" swe_status swe_adjoint(swe_ctx* c, int32_t nsteps, const int64_t* gau
     if (nsteps < 0 || ngauges < 0 || (ngauges > 0 && (!gauges || !obs)) || !loss || checkpoint_every < 0)
         return afail(c, SWE_ERR_ARG, "bad adjoint arguments");
     if (c->p.kappa != 0.0) return afail(c, SWE_ERR_UNSUPPORTED, "the adjoint needs kappa = 0");
+    if (c->p.friction != 0 || c->p.dissipation != 0)
+        return afail(c, SWE_ERR_UNSUPPORTED, "the adjoint differentiates the default friction and dissipation forms");
     if (c->p.kernel != SWE_KERNEL_FUSED && c->p.kernel != SWE_KERNEL_PLAIN)
         return afail(c, SWE_ERR_UNSUPPORTED, "the adjoint runs with the fused or the plain step");
     const long long ncell = (long long)c->p.nx * c->p.ny;

@@ -56,6 +56,9 @@ bool params_ok(const swe_params* p, char* why, size_t n) {
     if (p->seg_rows < 0 || p->seg_rows > 4096 || p->cta_warps < 0 || p->cta_warps > 16) {
         snprintf(why, n, "bad seg_rows / cta_warps"); return false;
     }
+    if (p->friction < 0 || p->friction > 1 || p->dissipation < 0 || p->dissipation > 1) {
+        snprintf(why, n, "friction and dissipation must be 0 or 1"); return false;
+    }
     return true;
 }
 
@@ -158,6 +161,8 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
     *out = nullptr;
     char why[256];
     if (!params_ok(p, why, sizeof(why))) return SWE_ERR_ARG;
+    // the ablation forms run in the plain and paper-layout kernels only
+    if ((p->friction != 0 || p->dissipation != 0) && p->kernel == SWE_KERNEL_FUSED) return SWE_ERR_UNSUPPORTED;
     swe_ctx* c = new (std::nothrow) swe_ctx();
     if (!c) return SWE_ERR_ARG;
     memset(c->err, 0, sizeof(c->err));

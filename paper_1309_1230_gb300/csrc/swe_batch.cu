@@ -550,6 +550,7 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
     if (!p || count < 1 || !nx || !ny || !manning_n) return SWE_ERR_ARG;
     if (p->precision != SWE_FP32) return SWE_ERR_UNSUPPORTED;
     if (p->dir_cycle != 0 && p->dir_cycle != 1) return SWE_ERR_UNSUPPORTED;
+    if (p->friction != 0 || p->dissipation != 0) return SWE_ERR_UNSUPPORTED;  // ablation forms: plain/paper only
     if (!(p->dx > 0) || !(p->dy > 0) || !(p->g > 0) || !(p->cfl > 0) || !(p->h_dry > 0) || !(p->dt_max > 0))
         return SWE_ERR_ARG;
     if (!(p->kappa >= 0) || !(p->kappa <= 0.25)) return SWE_ERR_ARG;

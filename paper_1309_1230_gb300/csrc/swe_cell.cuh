@@ -49,6 +49,9 @@ struct GridK {
     // copied from a neighbouring strip of a decomposed domain: they are
     // stepped like any row but enter no tally and no CFL maximum.
     int own_lo = 0, own_hi = 1 << 30;
+    // Ablation forms (plain and paper-layout kernels): explicit friction, and
+    // the TVD-MacCormack term in place of S15's switch form.
+    int friction = 0, dissipation = 0;
 };
 
 // Step constants, rounded from the FP64 step size.
@@ -370,8 +373,9 @@ __device__ __forceinline__ R continuity(R e0, R fe, R fw, R fn, R fs, const Step
 
 // Momentum of one stage (S7/S13): advection and the wet/dry-aware pressure
 // gradient from the one-sided differences in directions DX/DY, with the
-// point-implicit friction of coefficient cf.
-template <int DX, int DY, class R, class T>
+// point-implicit friction of coefficient cf (FR = 1: explicit friction,
+// vel0 - dt A - dt cf vel, the ablation form).
+template <int DX, int DY, int FR = 0, class R, class T>
 __device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn, R cf, R u0, R v0,
                                          const StepK<T>& S, T h_dry, R& uo, R& vo) {
     const R ex = eta_seen(xn, c.e, h_dry);
@@ -383,18 +387,24 @@ __device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, co
     else        { duy = c.u - yn.u; dvy = c.v - yn.v; dey = c.e - ey; }
     const R au = fma_(c.u, R(S.dtdx) * dux, fma_(c.v, R(S.dtdy) * duy, R(S.g_dtdx) * dex));
     const R av = fma_(c.u, R(S.dtdx) * dvx, fma_(c.v, R(S.dtdy) * dvy, R(S.g_dtdy) * dey));
+    if (FR == 1) {
+        const R dc = R(S.dt) * cf;
+        uo = fma_(-dc, c.u, u0 - au);
+        vo = fma_(-dc, c.v, v0 - av);
+        return;
+    }
     const R r = rcp_(fma_(R(S.dt), cf, R(T(1))));
     uo = smul(u0 - au, r);
     vo = smul(v0 - av, r);
 }
 
-template <int DX, int DY, class R, class T>
+template <int DX, int DY, int FR = 0, class R, class T>
 __device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn,
                                       R fe, R fw, R fn, R fs, R e0, R u0, R v0, R gn2,
                                       const StepK<T>& S, T h_dry, R& eo, R& uo, R& vo) {
     eo = continuity(e0, fe, fw, fn, fs, S);
     const R cf = friction(c, gn2, h_dry);
-    momentum<DX, DY>(c, xn, yn, cf, u0, v0, S, h_dry, uo, vo);
+    momentum<DX, DY, FR>(c, xn, yn, cf, u0, v0, S, h_dry, uo, vo);
 }
 
 // Wet/dry fix (S8/S16): negative depth -> eta = z (returns the added depth),

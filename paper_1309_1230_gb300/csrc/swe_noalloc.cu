@@ -76,6 +76,7 @@ extern "C" swe_status swe_step_plain_f32_noalloc(const swe_params* p, const floa
         return SWE_ERR_ARG;
     if (!(p->kappa >= 0) || !(p->kappa <= 0.25) || !(p->manning_n >= 0)) return SWE_ERR_ARG;
     if (p->dir_cycle < 0 || p->dir_cycle > 7) return SWE_ERR_ARG;
+    if (p->friction != 0 || p->dissipation != 0) return SWE_ERR_UNSUPPORTED;  // the ablation forms
     for (int s = 0; s < 4; ++s)
         if (p->bc[s] < SWE_BC_WALL || p->bc[s] > SWE_BC_OUTFLOW) return SWE_ERR_ARG;
     if (!(dt_fixed >= 0)) return SWE_ERR_ARG;

@@ -38,6 +38,15 @@ namespace pp {
 
 constexpr int BX = 256;  // threads per block, along a row
 
+template <int V>
+struct IntC {
+    static constexpr int value = V;
+};
+template <int X, int Y>
+struct Dirs {
+    static constexpr int x = X, y = Y;
+};
+
 template <class T>
 struct Ghosts {  // ghost cells of one level, per side (W/E: ny entries, S/N: nx)
     Cell<T>* side[4];
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(BX) k_friction(GridK<T> G, const T* __restrict
 
 // S7 / S13: momentum differenced on level (e, u, v) in directions (DX, DY),
 // updating the level-n velocities u0, v0.
-template <class T, int DX, int DY>
+template <class T, int DX, int DY, int FR>
 __global__ void __launch_bounds__(BX) k_momentum(GridK<T> G, const double* __restrict__ dtp, double dx, double dy,
                                                  double g, const T* __restrict__ e, const T* __restrict__ u,
                                                  const T* __restrict__ v, const T* __restrict__ z, Ghosts<T> gh,
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(BX) k_momentum(GridK<T> G, const double* __res
     const Cell<T> xn = nbr<DX, 0>(G, e, u, v, z, gh, i, j, k);
     const Cell<T> yn = nbr<0, DY>(G, e, u, v, z, gh, i, j, k);
     T a, b;
-    momentum<DX, DY>(c, xn, yn, C[k], u0[k], v0[k], S, G.h_dry, a, b);
+    momentum<DX, DY, FR>(c, xn, yn, C[k], u0[k], v0[k], S, G.h_dry, a, b);
     uo[k] = a;
     vo[k] = b;
 }
@@ -219,16 +228,19 @@ __global__ void __launch_bounds__(BX) k_average(GridK<T> G, const T* __restrict_
     v1[k] = T(0.5) * (vs[k] + vc[k]);
 }
 
-// S15: dissipation of level n added to the new level.
+// S15: dissipation of level n added to the new level (or the TVD term of
+// the ablation).
 template <class T>
-__global__ void __launch_bounds__(BX) k_dissipation(GridK<T> G, const T* __restrict__ e, const T* __restrict__ u,
+__global__ void __launch_bounds__(BX) k_dissipation(GridK<T> G, const double* __restrict__ dtp, double dx, double dy,
+                                                    double g, const T* __restrict__ e, const T* __restrict__ u,
                                                     const T* __restrict__ v, const T* __restrict__ z,
                                                     T* __restrict__ e1, T* __restrict__ u1, T* __restrict__ v1) {
     int i, j;
     if (!cell_of(G.nx, G.ny, i, j)) return;
     const size_t k = (size_t)j * G.pitch + i;
     T a = e1[k], b = u1[k], d = v1[k];
-    dissipation_at(G, i, j, e, u, v, z, e[k], u[k], v[k], z[k], a, b, d);
+    if (G.dissipation == 1) tvd_at(G, make_stepk<T>(*dtp, dx, dy, g), i, j, e, u, v, z, a, b, d);
+    else dissipation_at(G, i, j, e, u, v, z, e[k], u[k], v[k], z[k], a, b, d);
     e1[k] = a; u1[k] = b; v1[k] = d;
 }
 
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(SB * SB) k_continuity_sh(GridK<T> G, const dou
 }
 
 // S7 / S13 with the block's cells and one halo column/row in shared memory.
-template <class T, int DX, int DY>
+template <class T, int DX, int DY, int FR>
 __global__ void __launch_bounds__(SB * SB) k_momentum_sh(GridK<T> G, const double* __restrict__ dtp, double dx,
                                                          double dy, double g, const T* __restrict__ e,
                                                          const T* __restrict__ u, const T* __restrict__ v,
@@ -378,20 +390,21 @@ __global__ void __launch_bounds__(SB * SB) k_momentum_sh(GridK<T> G, const doubl
     const Cell<T> xn = (txn >= 0 && txn < SB) ? sc[ty][txn] : hx[ty];
     const Cell<T> yn = (tyn >= 0 && tyn < SB) ? sc[tyn][tx] : hy[tx];
     T a, b;
-    momentum<DX, DY>(sc[ty][tx], xn, yn, C[k], u0[k], v0[k], S, G.h_dry, a, b);
+    momentum<DX, DY, FR>(sc[ty][tx], xn, yn, C[k], u0[k], v0[k], S, G.h_dry, a, b);
     uo[k] = a;
     vo[k] = b;
 }
 
-// S15 with the block's depths (halo 2) and e, u, v (halo 1) in shared
-// memory, each at the clamped grid position the global form reads.
+// S15 (or the TVD term) with the block's depths and e, u, v (halo 2) in
+// shared memory, each at the clamped grid position the global form reads.
 template <class T>
-__global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const T* __restrict__ e,
+__global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const double* __restrict__ dtp, double dx,
+                                                            double dy, double g, const T* __restrict__ e,
                                                             const T* __restrict__ u, const T* __restrict__ v,
                                                             const T* __restrict__ z, T* __restrict__ e1,
                                                             T* __restrict__ u1, T* __restrict__ v1) {
     __shared__ T sh[SB + 4][SB + 4];
-    __shared__ T sf[3][SB + 2][SB + 2];
+    __shared__ T sf[3][SB + 4][SB + 4];
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * SB + tx;
     const int i0 = blockIdx.x * SB, j0 = blockIdx.y * SB;
     auto clampx = [&](int x) { return x < 0 ? 0 : (x >= G.nx ? G.nx - 1 : x); };
@@ -401,9 +414,9 @@ __global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const T*
         const size_t k = (size_t)clampy(j0 + r - 2) * G.pitch + clampx(i0 + c - 2);
         sh[r][c] = e[k] - z[k];
     }
-    for (int q = t; q < (SB + 2) * (SB + 2); q += SB * SB) {
-        const int r = q / (SB + 2), c = q % (SB + 2);
-        const size_t k = (size_t)clampy(j0 + r - 1) * G.pitch + clampx(i0 + c - 1);
+    for (int q = t; q < (SB + 4) * (SB + 4); q += SB * SB) {
+        const int r = q / (SB + 4), c = q % (SB + 4);
+        const size_t k = (size_t)clampy(j0 + r - 2) * G.pitch + clampx(i0 + c - 2);
         sf[0][r][c] = e[k];
         sf[1][r][c] = u[k];
         sf[2][r][c] = v[k];
@@ -413,10 +426,13 @@ __global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const T*
     if (i >= G.nx || j >= G.ny) return;
     const size_t k = (size_t)j * G.pitch + i;
     auto hat = [&](int ii, int jj) -> T { return sh[jj - j0 + 2][ii - i0 + 2]; };
-    auto atf = [&](int f, int ii, int jj) -> T { return sf[f][jj - j0 + 1][ii - i0 + 1]; };
+    auto atf = [&](int f, int ii, int jj) -> T { return sf[f][jj - j0 + 2][ii - i0 + 2]; };
     T a = e1[k], b = u1[k], d = v1[k];
-    dissipation_core(G, i, j, hat, atf, sf[0][ty + 1][tx + 1], sf[1][ty + 1][tx + 1], sf[2][ty + 1][tx + 1], z[k], a,
-                     b, d);
+    if (G.dissipation == 1)
+        tvd_core(G, make_stepk<T>(*dtp, dx, dy, g), i, j, hat, atf, a, b, d);
+    else
+        dissipation_core(G, i, j, hat, atf, sf[0][ty + 2][tx + 2], sf[1][ty + 2][tx + 2], sf[2][ty + 2][tx + 2], z[k], a,
+                         b, d);
     e1[k] = a; u1[k] = b; v1[k] = d;
 }
 
@@ -538,12 +554,19 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
     else
         k_continuity<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qx, q->qy, q->gn, q->es);  // S5
     k_friction<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, n2, q->C);                                    // S6
-    if (shared)
-        k_momentum_sh<T, SX, SY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, q->gn, q->C, u, v,
-                                                               q->us, q->vs);
-    else
-        k_momentum<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, q->gn, q->C, u, v, q->us,
-                                                          q->vs);                                          // S7
+    // S7 (FR: the friction form)
+    auto mom = [&](auto fr, const T* me, const T* mu, const T* mv, const Ghosts<T>& mg, const T* mC, T* ou, T* ov,
+                   auto dirs) {
+        constexpr int F = decltype(fr)::value, MX = decltype(dirs)::x, MY = decltype(dirs)::y;
+        if (shared)
+            k_momentum_sh<T, MX, MY, F><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, me, mu, mv, z, mg, mC, u,
+                                                                      v, ou, ov);
+        else
+            k_momentum<T, MX, MY, F><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, me, mu, mv, z, mg, mC, u, v,
+                                                                 ou, ov);
+    };
+    if (p.friction == 1) mom(IntC<1>(), e, u, v, q->gn, q->C, q->us, q->vs, Dirs<SX, SY>());
+    else mom(IntC<0>(), e, u, v, q->gn, q->C, q->us, q->vs, Dirs<SX, SY>());
     k_fix_pred<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, c->ctl, area);                    // S8
     k_ghosts<T><<<gb, 256, 0, c->stream>>>(G, q->es, q->us, q->vs, z, q->gs);                              // S9
     k_fluxes<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, q->qxs, q->qys);                    // S10
@@ -554,16 +577,12 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
         k_continuity<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, q->qxs, q->qys, q->gs,
                                                             q->ec);                                        // S11
     k_friction<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, z, n2, q->Cs);                       // S12
-    if (shared)
-        k_momentum_sh<T, CX, CY><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, q->es, q->us, q->vs, z, q->gs,
-                                                               q->Cs, u, v, q->uc, q->vc);
-    else
-        k_momentum<T, CX, CY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, q->es, q->us, q->vs, z, q->gs,
-                                                          q->Cs, u, v, q->uc, q->vc);                      // S13
+    if (p.friction == 1) mom(IntC<1>(), q->es, q->us, q->vs, q->gs, q->Cs, q->uc, q->vc, Dirs<CX, CY>());  // S13
+    else mom(IntC<0>(), q->es, q->us, q->vs, q->gs, q->Cs, q->uc, q->vc, Dirs<CX, CY>());
     k_average<T><<<grd, blk, 0, c->stream>>>(G, q->es, q->us, q->vs, q->ec, q->uc, q->vc, e1, u1, v1);     // S14
-    if (p.kappa != 0.0) {                                                                                  // S15
-        if (shared) k_dissipation_sh<T><<<sgrd, sblk, 0, c->stream>>>(G, e, u, v, z, e1, u1, v1);
-        else k_dissipation<T><<<grd, blk, 0, c->stream>>>(G, e, u, v, z, e1, u1, v1);
+    if (p.kappa != 0.0 || p.dissipation == 1) {                                                            // S15
+        if (shared) k_dissipation_sh<T><<<sgrd, sblk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, e1, u1, v1);
+        else k_dissipation<T><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, e, u, v, z, e1, u1, v1);
     }
     k_final<T><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, e, u, v, z, q->qxs, q->qys, e1, u1, v1, c->ctl,
                                            devdt ? 1 : 0, slot_next, area);                                // S16

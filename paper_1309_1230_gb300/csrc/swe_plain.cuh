@@ -90,7 +90,84 @@ __device__ __forceinline__ void dissipation_at(const GridK<T>& G, int i, int j, 
     dissipation_core(G, i, j, hat, at, e0, u0, v0, zc, en, un, vn);
 }
 
-template <class T, int SX, int SY>
+// The TVD-MacCormack term (the ablation form of S15; Davis 1984, for shallow
+// water Garcia-Navarro, Alcrudo and Saviron 1992) at cell (i, j), per axis
+// and field phi of level n, with D the face differences (0 beyond the grid,
+// which clamped accessors give):
+//   r+_i = D_{i-1/2} D_{i+1/2} / D_{i+1/2}^2, r-_i = D_{i-1/2} D_{i+1/2} / D_{i-1/2}^2 (0 on a zero denominator),
+//   psi(r) = max(0, min(2 r, 1)), C(nu) = nu (1 - nu) up to nu = 1/2, then 1/4,
+//   nu = (|vel| + sqrt(g h)) dt / dx on a wet cell (0 on a dry one), G = C (1 - psi) / 2,
+//   T_{i+1/2} = (G(nu_i, r+_i) + G(nu_{i+1}, r-_{i+1})) D_{i+1/2} between two wet
+// interior cells; phi += (T_e - T_w) + (T_n - T_s).
+template <class T>
+__device__ __forceinline__ T tvd_psi(T r) {
+    T m = r + r;
+    m = m < T(1) ? m : T(1);
+    return m > T(0) ? m : T(0);
+}
+template <class T>
+__device__ __forceinline__ T tvd_cnu(T nu) { return nu <= T(0.5) ? nu * (T(1) - nu) : T(0.25); }
+template <class T>
+__device__ __forceinline__ T tvd_ratio(T num, T den) { return den != T(0) ? div_(num, den) : T(0); }
+template <class T>
+__device__ __forceinline__ T tvd_face(T dm, T d, T dp, T nua, T nub) {
+    const T rpa = tvd_ratio(dm * d, d * d);
+    const T rmb = tvd_ratio(d * dp, d * d);
+    const T ga = T(0.5) * tvd_cnu(nua) * (T(1) - tvd_psi(rpa));
+    const T gb = T(0.5) * tvd_cnu(nub) * (T(1) - tvd_psi(rmb));
+    return (ga + gb) * d;
+}
+
+template <class T, class HAT, class AT>
+__device__ __forceinline__ void tvd_core(const GridK<T>& G, const StepK<T>& S, int i, int j, HAT&& hat, AT&& at,
+                                         T& en, T& un, T& vn) {
+    const T hd = G.h_dry;
+    auto nux = [&](int ii) -> T {
+        const T h = hat(ii, j);
+        return h > hd ? (fabs(at(1, ii, j)) + rsq_sqrt(G.g * h)) * S.dtdx : T(0);
+    };
+    auto nuy = [&](int jj) -> T {
+        const T h = hat(i, jj);
+        return h > hd ? (fabs(at(2, i, jj)) + rsq_sqrt(G.g * h)) * S.dtdy : T(0);
+    };
+    const bool wc = hat(i, j) > hd;
+    const bool we = i + 1 < G.nx && wc && hat(i + 1, j) > hd, ww = i - 1 >= 0 && wc && hat(i - 1, j) > hd;
+    const bool wn = j + 1 < G.ny && wc && hat(i, j + 1) > hd, ws = j - 1 >= 0 && wc && hat(i, j - 1) > hd;
+    const T nxc = nux(i), nxe = nux(i + 1), nxw = nux(i - 1);
+    const T nyc = nuy(j), nyn = nuy(j + 1), nys = nuy(j - 1);
+    T* out[3] = {&en, &un, &vn};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        auto Dx = [&](int ii) -> T { return at(f, ii + 1, j) - at(f, ii, j); };
+        auto Dy = [&](int jj) -> T { return at(f, i, jj + 1) - at(f, i, jj); };
+        const T te = we ? tvd_face(Dx(i - 1), Dx(i), Dx(i + 1), nxc, nxe) : T(0);
+        const T tw = ww ? tvd_face(Dx(i - 2), Dx(i - 1), Dx(i), nxw, nxc) : T(0);
+        const T tn = wn ? tvd_face(Dy(j - 1), Dy(j), Dy(j + 1), nyc, nyn) : T(0);
+        const T ts = ws ? tvd_face(Dy(j - 2), Dy(j - 1), Dy(j), nys, nyc) : T(0);
+        *out[f] = *out[f] + ((te - tw) + (tn - ts));
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void tvd_at(const GridK<T>& G, const StepK<T>& S, int i, int j, const T* __restrict__ e,
+                                       const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ z,
+                                       T& en, T& un, T& vn) {
+    auto hat = [&](int ii, int jj) -> T {
+        ii = ii < 0 ? 0 : (ii >= G.nx ? G.nx - 1 : ii);
+        jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
+        size_t q = (size_t)jj * G.pitch + ii;
+        return e[q] - z[q];
+    };
+    auto at = [&](int f, int ii, int jj) -> T {
+        ii = ii < 0 ? 0 : (ii >= G.nx ? G.nx - 1 : ii);
+        jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
+        const T* p = f == 0 ? e : (f == 1 ? u : v);
+        return p[(size_t)jj * G.pitch + ii];
+    };
+    tvd_core(G, S, i, j, hat, at, en, un, vn);
+}
+
+template <class T, int SX, int SY, int FR = 0>
 __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __restrict__ dtp, double dx,
                                                     double dy, double g, const T* __restrict__ e,
                                                     const T* __restrict__ u, const T* __restrict__ v,
@@ -113,7 +190,7 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __
         faces<SX>((c.e - c.z) * c.u, (xn.e - xn.z) * xn.u, i == 0, i == G.nx - 1, SIDE_W, SIDE_E, G, fe, fw);
         faces<SY>((c.e - c.z) * c.v, (yn.e - yn.z) * yn.v, j == 0, j == G.ny - 1, SIDE_S, SIDE_N, G, fn, fs);
         T eo, uo, vo;
-        stage<SX, SY>(c, xn, yn, fe, fw, fn, fs, c.e, c.u, c.v, gn2, S, G.h_dry, eo, uo, vo);
+        stage<SX, SY, FR>(c, xn, yn, fe, fw, fn, fs, c.e, c.u, c.v, gn2, S, G.h_dry, eo, uo, vo);
         added = wetdry_fix(eo, uo, vo, c.z, G.h_dry);
         es[k] = eo; us[k] = uo; vs[k] = vo;
         if (j < G.own_lo || j >= G.own_hi) added = T(0);
@@ -125,7 +202,7 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __
     }
 }
 
-template <class T, int SX, int SY>
+template <class T, int SX, int SY, int FR = 0>
 __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, const double* __restrict__ dtp,
                                                     double dx, double dy, double g,
                                                     const T* __restrict__ e, const T* __restrict__ u,
@@ -157,11 +234,12 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, con
         faces<CX>(qxs, (xs.e - xs.z) * xs.u, i == 0, i == G.nx - 1, SIDE_W, SIDE_E, G, fe, fw);
         faces<CY>(qys, (ys.e - ys.z) * ys.v, j == 0, j == G.ny - 1, SIDE_S, SIDE_N, G, fn, fs);
         T eo, uo, vo;
-        stage<CX, CY>(cs, xs, ys, fe, fw, fn, fs, e0, u0, v0, gn2, S, G.h_dry, eo, uo, vo);
+        stage<CX, CY, FR>(cs, xs, ys, fe, fw, fn, fs, e0, u0, v0, gn2, S, G.h_dry, eo, uo, vo);
         // S14: average
         T en = T(0.5) * (cs.e + eo), un = T(0.5) * (cs.u + uo), vn = T(0.5) * (cs.v + vo);
-        // S15: dissipation of level n
-        if (G.kappa != T(0)) dissipation_at(G, i, j, e, u, v, z, e0, u0, v0, zc, en, un, vn);
+        // S15: dissipation of level n (or the TVD term of the ablation)
+        if (G.dissipation == 1) tvd_at(G, S, i, j, e, u, v, z, en, un, vn);
+        else if (G.kappa != T(0)) dissipation_at(G, i, j, e, u, v, z, e0, u0, v0, zc, en, un, vn);
         // S16: fix, tallies
         added = wetdry_fix(en, un, vn, zc, G.h_dry);
         e1[k] = en; u1[k] = un; v1[k] = vn;
@@ -204,10 +282,11 @@ static GridK<T> grid_of(const swe_ctx* c) {
     G.inv_dx = (T)(1.0 / p.dx); G.inv_dy = (T)(1.0 / p.dy);
     for (int s = 0; s < 4; ++s) { G.bc[s] = p.bc[s]; G.qin[s] = (T)p.q_in[s]; }
     G.own_lo = c->own_lo; G.own_hi = c->own_hi;
+    G.friction = p.friction; G.dissipation = p.dissipation;
     return G;
 }
 
-template <class T, int SX, int SY>
+template <class T, int SX, int SY, int FR>
 static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
     const swe_params& p = c->p;
     GridK<T> G = grid_of<T>(c);
@@ -217,10 +296,10 @@ static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const int a = c->cur, b = 1 - c->cur;
     const double area = p.dx * p.dy;
-    k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(
+    k_plain_pred<T, SX, SY, FR><<<grd, blk, 0, c->stream>>>(
         G, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (T*)c->ps[0], (T*)c->ps[1], (T*)c->ps[2], c->ctl, area);
-    k_plain_corr<T, SX, SY><<<grd, blk, 0, c->stream>>>(
+    k_plain_corr<T, SX, SY, FR><<<grd, blk, 0, c->stream>>>(
         G, c->ctl, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (const T*)c->ps[0], (const T*)c->ps[1], (const T*)c->ps[2], (T*)c->eta[b], (T*)c->u[b],
         (T*)c->v[b], slot_next, area);
@@ -231,10 +310,16 @@ template <class T>
 static cudaError_t plain_step_dir(swe_ctx* c, int s, long long k) {
     int sx, sy;
     step_dirs(c->p.dir_cycle, k, &sx, &sy);
-    if (sx > 0 && sy > 0) return plain_step_t<T, 1, 1>(c, s, k);
-    if (sx > 0 && sy < 0) return plain_step_t<T, 1, -1>(c, s, k);
-    if (sx < 0 && sy > 0) return plain_step_t<T, -1, 1>(c, s, k);
-    return plain_step_t<T, -1, -1>(c, s, k);
+    if (c->p.friction == 1) {  // the explicit-friction ablation
+        if (sx > 0 && sy > 0) return plain_step_t<T, 1, 1, 1>(c, s, k);
+        if (sx > 0 && sy < 0) return plain_step_t<T, 1, -1, 1>(c, s, k);
+        if (sx < 0 && sy > 0) return plain_step_t<T, -1, 1, 1>(c, s, k);
+        return plain_step_t<T, -1, -1, 1>(c, s, k);
+    }
+    if (sx > 0 && sy > 0) return plain_step_t<T, 1, 1, 0>(c, s, k);
+    if (sx > 0 && sy < 0) return plain_step_t<T, 1, -1, 0>(c, s, k);
+    if (sx < 0 && sy > 0) return plain_step_t<T, -1, 1, 0>(c, s, k);
+    return plain_step_t<T, -1, -1, 0>(c, s, k);
 }
 
 }  // namespace swe

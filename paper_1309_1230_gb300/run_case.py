@@ -30,6 +30,9 @@ def main(argv=None):
                     choices=["fused", "plain", "paper", "paper_devdt", "paper_shared", "paper_shared_devdt"])
     ap.add_argument("--seg-rows", type=int, default=0, help="rows per work item (0: automatic)")
     ap.add_argument("--dry-skip", type=int, default=1, choices=[0, 1], help="skip all-dry work items")
+    ap.add_argument("--kappa", type=float, default=None, help="S15 coefficient (default: the case's)")
+    ap.add_argument("--friction", type=int, default=0, choices=[0, 1], help="1: explicit friction (ablation)")
+    ap.add_argument("--dissipation", type=int, default=0, choices=[0, 1], help="1: the TVD term (ablation)")
     a = ap.parse_args(argv)
 
     import torch
@@ -49,8 +52,10 @@ def main(argv=None):
     kern = {"fused": swe.SWE_KERNEL_FUSED, "plain": swe.SWE_KERNEL_PLAIN, "paper": swe.SWE_KERNEL_PAPER,
             "paper_devdt": swe.SWE_KERNEL_PAPER_DEVDT, "paper_shared": swe.SWE_KERNEL_PAPER_SHARED,
             "paper_shared_devdt": swe.SWE_KERNEL_PAPER_SHARED_DEVDT}[a.kernel]
-    s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=case["kappa"], bc=case["bc"],
-                   q_in=case["q_in"], precision=prec, kernel=kern, seg_rows=a.seg_rows, dry_skip=a.dry_skip)
+    kappa = case["kappa"] if a.kappa is None else a.kappa
+    s = swe.Solver(case["nx"], case["ny"], manning_n=case["manning_n"], kappa=kappa, bc=case["bc"],
+                   q_in=case["q_in"], precision=prec, kernel=kern, seg_rows=a.seg_rows, dry_skip=a.dry_skip,
+                   friction=a.friction, dissipation=a.dissipation)
     s.set_bed(case["z"])
     s.set_state(case["eta"], case["u"], case["v"])
     s.step(a.warmup, want_info=False)
@@ -64,7 +69,8 @@ def main(argv=None):
     ms = e0.elapsed_time(e1) / max(1, a.steps)
     info = s.info()
     print(json.dumps({"case": a.case, "n": a.n, "precision": a.precision, "kernel": a.kernel, "steps": a.steps,
-                      "seg_rows": a.seg_rows, "dry_skip": a.dry_skip,
+                      "seg_rows": a.seg_rows, "dry_skip": a.dry_skip, "kappa": kappa, "friction": a.friction,
+                      "dissipation": a.dissipation,
                       "ms_per_step": ms, "cell_updates_per_s": case["nx"] * case["ny"] / (ms / 1e3),
                       "volume": info.volume, "t": info.t, "time": time.time()}))
     s.close()

@@ -43,7 +43,8 @@ class swe_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("seg_rows", ctypes.c_int32), ("cta_warps", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("dry_skip", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("friction", ctypes.c_int32), ("dissipation", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -156,7 +157,7 @@ def _f64(a, shape):
 def make_params(nx, ny, *, dx=1.0, dy=1.0, g=9.81, cfl=0.5, h_dry=1e-3, dt_max=10.0, kappa=0.0,
                 manning_n=0.0, bc=(0, 0, 0, 0), q_in=(0.0, 0.0, 0.0, 0.0), precision=SWE_FP64,
                 dir_cycle=1, device=0, kernel=SWE_KERNEL_FUSED, stream=None, seg_rows=0, cta_warps=0,
-                use_graph=1, dry_skip=1, reserved=(0, 0, 0, 0)) -> swe_params:
+                use_graph=1, dry_skip=1, friction=0, dissipation=0, reserved=(0, 0)) -> swe_params:
     p = swe_params()
     load().swe_params_default(ctypes.byref(p))
     p.nx, p.ny, p.dx, p.dy, p.g, p.cfl = int(nx), int(ny), dx, dy, g, cfl
@@ -167,7 +168,8 @@ def make_params(nx, ny, *, dx=1.0, dy=1.0, g=9.81, cfl=0.5, h_dry=1e-3, dt_max=1
     p.precision, p.dir_cycle, p.device, p.kernel = int(precision), int(dir_cycle), int(device), int(kernel)
     p.stream = stream
     p.seg_rows, p.cta_warps, p.use_graph, p.dry_skip = int(seg_rows), int(cta_warps), int(use_graph), int(dry_skip)
-    for q in range(4):
+    p.friction, p.dissipation = int(friction), int(dissipation)
+    for q in range(2):
         p.reserved[q] = int(reserved[q])
     return p
 
