@@ -498,14 +498,15 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
     ACK(buf.get(&ggn2, plane * sizeof(T)));
     ACK(buf.get(&ggz, plane * sizeof(T)));
     long long* gd = nullptr;
-    double *gv = nullptr, *res = nullptr, *dtd = nullptr;
+    double *gv = nullptr, *res = nullptr;
+    StepSlot* ssd = nullptr;  // per step: the frozen step size and its constants (the recompute kernels read them)
     DevCtl* ctl = nullptr;
     unsigned* dry = nullptr;
     ACK(buf.get(&dry, sizeof(unsigned)));
     ACK(buf.get(&gd, (ng > 0 ? ng : 1) * sizeof(long long)));
     ACK(buf.get(&gv, (size_t)(T_ > 0 ? T_ : 1) * (ng > 0 ? ng : 1) * sizeof(double)));
     ACK(buf.get(&res, (size_t)(T_ > 0 ? T_ : 1) * (ng > 0 ? ng : 1) * sizeof(double)));
-    ACK(buf.get(&dtd, (size_t)(T_ > 0 ? T_ : 1) * sizeof(double)));
+    ACK(buf.get(&ssd, (size_t)(T_ > 0 ? T_ : 1) * sizeof(StepSlot)));
     ACK(buf.get(&ctl, sizeof(DevCtl)));
     if (ng > 0) ACK(cudaMemcpyAsync(gd, gauges, ng * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
 
@@ -560,7 +561,6 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
         ACK(cudaGetLastError());
         c->step += T_;
         ACK(cudaMemcpyAsync(dts.data(), c->dt_hist, (size_t)T_ * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        ACK(cudaMemcpyAsync(dtd, c->dt_hist, (size_t)T_ * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
     std::vector<double> g((size_t)(T_ > 0 ? T_ : 1) * (ng > 0 ? ng : 1));
     if (T_ > 0 && ng > 0)
@@ -575,6 +575,10 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
         }
     if (!std::isfinite(L)) return afail(c, SWE_ERR_NONFINITE, "non-finite loss");
     *loss = L;
+    std::vector<StepSlot> slots(T_ > 0 ? T_ : 1);
+    for (int s = 0; s < T_; ++s) slots[s] = make_slot(dts[s], p.dx, p.dy, p.g);
+    if (T_ > 0)
+        ACK(cudaMemcpyAsync(ssd, slots.data(), (size_t)T_ * sizeof(StepSlot), cudaMemcpyHostToDevice, c->stream));
     if (T_ > 0 && ng > 0)
         ACK(cudaMemcpyAsync(res, g.data(), (size_t)T_ * ng * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 
@@ -591,9 +595,9 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
             cudaMemcpyAsync(seg[0].u, cp[sg].u, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
             cudaMemcpyAsync(seg[0].v, cp[sg].v, plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
             for (int s = s0; s + 1 < s1; ++s)
-                dispatch_plain<T>(c, G, step0 + s, ctl, dtd + s, seg[s - s0], qs, seg[s - s0 + 1]);
+                dispatch_plain<T>(c, G, step0 + s, ctl, &ssd[s].dt, seg[s - s0], qs, seg[s - s0 + 1]);
             for (int s = s1 - 1; s >= s0; --s) {
-                dispatch_adj<T>(c, G, step0 + s, dts[s], ctl, dtd + s, seg[s - s0], qs, lam, Sc, GX, GY, Bc, Pc, PX,
+                dispatch_adj<T>(c, G, step0 + s, dts[s], ctl, &ssd[s].dt, seg[s - s0], qs, lam, Sc, GX, GY, Bc, Pc, PX,
                                 PY, ggn2, ggz, dry);
                 if (s >= 1 && ng > 0)
                     k_gauge_add<T><<<1, 1, 0, c->stream>>>(lam.e, gd, ng, p.nx, c->pitch, res + (size_t)(s - 1) * ng);

@@ -71,6 +71,37 @@ __host__ __device__ inline StepK<T> make_stepk(double dt, double dx, double dy, 
     return s;
 }
 
+// The step size with its constants in both real types, computed once per
+// step by one thread (or on the host) from the same FP64 step size: kernels
+// that run one thread per cell read them here instead of dividing in FP64 in
+// every thread (GB300's FP64 rate is a small fraction of its FP32 rate).  A
+// pointer to `dt` is a pointer to the slot.
+struct StepSlot {
+    double dt;
+    StepK<float> f;
+    StepK<double> d;
+};
+
+__host__ __device__ inline StepSlot make_slot(double dt, double dx, double dy, double g) {
+    StepSlot s;
+    s.dt = dt;
+    s.f = make_stepk<float>(dt, dx, dy, g);
+    s.d = make_stepk<double>(dt, dx, dy, g);
+    return s;
+}
+
+// The constants of the slot whose step size dtp points at.
+template <class T>
+__device__ __forceinline__ StepK<T> step_consts(const double* dtp);
+template <>
+__device__ __forceinline__ StepK<float> step_consts<float>(const double* dtp) {
+    return reinterpret_cast<const StepSlot*>(dtp)->f;
+}
+template <>
+__device__ __forceinline__ StepK<double> step_consts<double>(const double* dtp) {
+    return reinterpret_cast<const StepSlot*>(dtp)->d;
+}
+
 // Scalar fused multiply-add, round to nearest (FP32: subnormals flushed,
 // stated explicitly so that the packed form below rounds the same).
 __device__ __forceinline__ float fma_(float a, float b, float c) {

@@ -17,7 +17,7 @@ struct DevCtl {
     double clamp, bflux[4];
     unsigned int flags;
     unsigned int pad;
-    double dt_cur;               // plain path: step size of the current step
+    StepSlot cur;                // plain and paper paths: step size and constants of the current step
     unsigned int qctr[3];        // fused path: work-queue counter, slot k%3 = step k
     unsigned int pad2;
 };

@@ -89,9 +89,9 @@ __device__ __forceinline__ Cell<T> nbr(const GridK<T>& G, const T* e, const T* u
 
 // Step size and clock bookkeeping of step s (S2's result on the device).
 __global__ void k_paper_dt(DevCtl* ctl, const double* dtv, int from_smax, int slot, int slot_next, int s,
-                           double* dt_hist, double cfl, double dt_max) {
+                           double* dt_hist, double cfl, double dt_max, double dx, double dy, double g) {
     const double dt = from_smax ? dt_from_speed(__longlong_as_double((long long)ctl->smax[slot]), cfl, dt_max) : *dtv;
-    ctl->dt_cur = dt;
+    ctl->cur = make_slot(dt, dx, dy, g);
     ctl->dt_last = dt;
     ctl->t += dt;
     ctl->dt_min = fmin(ctl->dt_min, dt);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(BX) k_continuity(GridK<T> G, const double* __r
                                                    const T* __restrict__ qy, Ghosts<T> gh, T* __restrict__ eo) {
     int i, j;
     if (!cell_of(G.nx, G.ny, i, j)) return;
-    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     const size_t k = (size_t)j * G.pitch + i;
     T qxn, qyn;
     if (i + DX >= 0 && i + DX < G.nx) qxn = qx[(size_t)((ptrdiff_t)k + DX)];
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(BX) k_momentum(GridK<T> G, const double* __res
                                                  const T* __restrict__ v0, T* __restrict__ uo, T* __restrict__ vo) {
     int i, j;
     if (!cell_of(G.nx, G.ny, i, j)) return;
-    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     const size_t k = (size_t)j * G.pitch + i;
     const Cell<T> c = at(e, u, v, z, k);
     const Cell<T> xn = nbr<DX, 0>(G, e, u, v, z, gh, i, j, k);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(BX) k_dissipation(GridK<T> G, const double* __
     if (!cell_of(G.nx, G.ny, i, j)) return;
     const size_t k = (size_t)j * G.pitch + i;
     T a = e1[k], b = u1[k], d = v1[k];
-    if (G.dissipation == 1) tvd_at(G, make_stepk<T>(*dtp, dx, dy, g), i, j, e, u, v, z, a, b, d);
+    if (G.dissipation == 1) tvd_at(G, step_consts<T>(dtp), i, j, e, u, v, z, a, b, d);
     else dissipation_at(G, i, j, e, u, v, z, e[k], u[k], v[k], z[k], a, b, d);
     e1[k] = a; u1[k] = b; v1[k] = d;
 }
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(SB * SB) k_continuity_sh(GridK<T> G, const dou
     if (ty == 0) sy[DY > 0 ? SB : 0][tx] = qyat(i, j0 + (DY > 0 ? SB : -1));
     __syncthreads();
     if (i >= G.nx || j >= G.ny) return;
-    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     const size_t k = (size_t)j * G.pitch + i;
     const T qxc = sx[ty][tx - XL], qxn = sx[ty][tx - XL + DX];
     const T qyc = sy[ty - YL][tx], qyn = sy[ty - YL + DY][tx];
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(SB * SB) k_momentum_sh(GridK<T> G, const doubl
     if (ty == 0) hy[tx] = cell_or_ghost(G, e, u, v, z, gh, i, j0 + (DY > 0 ? SB : -1));
     __syncthreads();
     if (i >= G.nx || j >= G.ny) return;
-    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     const size_t k = (size_t)j * G.pitch + i;
     const int txn = tx + DX, tyn = ty + DY;
     const Cell<T> xn = (txn >= 0 && txn < SB) ? sc[ty][txn] : hx[ty];
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(SB * SB) k_dissipation_sh(GridK<T> G, const do
     auto atf = [&](int f, int ii, int jj) -> T { return sf[f][jj - j0 + 2][ii - i0 + 2]; };
     T a = e1[k], b = u1[k], d = v1[k];
     if (G.dissipation == 1)
-        tvd_core(G, make_stepk<T>(*dtp, dx, dy, g), i, j, hat, atf, a, b, d);
+        tvd_core(G, step_consts<T>(dtp), i, j, hat, atf, a, b, d);
     else
         dissipation_core(G, i, j, hat, atf, sf[0][ty + 2][tx + 2], sf[1][ty + 2][tx + 2], sf[2][ty + 2][tx + 2], z[k], a,
                          b, d);
@@ -541,8 +541,8 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
             return err;
     }
     k_paper_dt<<<1, 1, 0, c->stream>>>(c->ctl, dtv, (!fixed && devdt) ? 1 : 0, slot, slot_next, s, c->dt_hist, p.cfl,
-                                       p.dt_max);
-    const double* dtp = &c->ctl->dt_cur;
+                                       p.dt_max, p.dx, p.dy, p.g);
+    const double* dtp = &c->ctl->cur.dt;
     const dim3 blk(BX), grd((p.nx + BX - 1) / BX, p.ny);
     const int nside = p.nx > p.ny ? p.nx : p.ny;
     const int gb = (nside + 255) / 256;

@@ -269,16 +269,16 @@ cudaError_t swe_plain_step_f32_raw(const swe_params* p, int pitch, const float* 
     for (int s = 0; s < 4; ++s) { G.bc[s] = p->bc[s]; G.qin[s] = (float)p->q_in[s]; }
     const size_t n = (size_t)p->nx * p->ny;
     if (!dt_fixed) k_prologue<float><<<util_blocks(n), 256, 0, st>>>(G, e, u, v, z, ctl, 0);
-    k_plain_dt<<<1, 1, 0, st>>>(ctl, 0, 1, dt_fixed, 0, dt_hist, p->cfl, p->dt_max);
+    k_plain_dt<<<1, 1, 0, st>>>(ctl, 0, 1, dt_fixed, 0, dt_hist, p->cfl, p->dt_max, p->dx, p->dy, p->g);
     int sx, sy;
     step_dirs(p->dir_cycle, 0, &sx, &sy);
     dim3 blk(32, 8), grd((p->nx + 31) / 32, (p->ny + 7) / 8);
     const double area = p->dx * p->dy;
 #define SWE_RAW_STEP(SX_, SY_)                                                                                   \
     do {                                                                                                         \
-        k_plain_pred<float, SX_, SY_><<<grd, blk, 0, st>>>(G, &ctl->dt_cur, p->dx, p->dy, p->g, e, u, v, z,     \
+        k_plain_pred<float, SX_, SY_><<<grd, blk, 0, st>>>(G, &ctl->cur.dt, p->dx, p->dy, p->g, e, u, v, z,     \
                                                            nullptr, ps_e, ps_u, ps_v, ctl, area);                \
-        k_plain_corr<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, &ctl->dt_cur, p->dx, p->dy, p->g, e, u, v, z, \
+        k_plain_corr<float, SX_, SY_><<<grd, blk, 0, st>>>(G, ctl, &ctl->cur.dt, p->dx, p->dy, p->g, e, u, v, z, \
                                                            nullptr, ps_e, ps_u, ps_v, e1, u1, v1, 1, area);      \
     } while (0)
     if (sx > 0 && sy > 0) SWE_RAW_STEP(1, 1);

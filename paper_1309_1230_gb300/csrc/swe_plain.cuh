@@ -30,11 +30,11 @@ __device__ __forceinline__ T warp_max(T x) {
 
 // Step size of step s of a call: replayed or from the level's CFL reduction.
 static __global__ void k_plain_dt(DevCtl* ctl, int slot, int slot_next, const double* dt_fixed, int s,
-                           double* dt_hist, double cfl, double dt_max) {
+                           double* dt_hist, double cfl, double dt_max, double dx, double dy, double g) {
     double dt;
     if (dt_fixed) dt = dt_fixed[s];
     else dt = dt_from_speed(__longlong_as_double((long long)ctl->smax[slot]), cfl, dt_max);
-    ctl->dt_cur = dt;
+    ctl->cur = make_slot(dt, dx, dy, g);
     ctl->dt_last = dt;
     ctl->t += dt;
     ctl->dt_min = fmin(ctl->dt_min, dt);
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_plain_pred(GridK<T> G, const double* __
                                                     T* __restrict__ vs, DevCtl* ctl_w, double area) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const StepK<T> S = make_stepk<T>(*dtp, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     T added = T(0);
     if (i < G.nx && j < G.ny) {
         const size_t k = (size_t)j * G.pitch + i;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_plain_corr(GridK<T> G, DevCtl* ctl, con
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const double dtd = *dtp;
-    const StepK<T> S = make_stepk<T>(dtd, dx, dy, g);
+    const StepK<T> S = step_consts<T>(dtp);
     T added = T(0), speed = T(0);
     double bw = 0.0, be = 0.0, bs = 0.0, bn = 0.0;
     bool bad = false;
@@ -292,15 +292,15 @@ static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
     GridK<T> G = grid_of<T>(c);
     int slot = (int)(k % 3), slot_next = (int)((k + 1) % 3);
     k_plain_dt<<<1, 1, 0, c->stream>>>(c->ctl, slot, slot_next, c->dt_fixed_cap > 0 && c->dt_fixed ? c->dt_fixed : nullptr,
-                                       s, c->dt_hist, p.cfl, p.dt_max);
+                                       s, c->dt_hist, p.cfl, p.dt_max, p.dx, p.dy, p.g);
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const int a = c->cur, b = 1 - c->cur;
     const double area = p.dx * p.dy;
     k_plain_pred<T, SX, SY, FR><<<grd, blk, 0, c->stream>>>(
-        G, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        G, &c->ctl->cur.dt, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (T*)c->ps[0], (T*)c->ps[1], (T*)c->ps[2], c->ctl, area);
     k_plain_corr<T, SX, SY, FR><<<grd, blk, 0, c->stream>>>(
-        G, c->ctl, &c->ctl->dt_cur, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
+        G, c->ctl, &c->ctl->cur.dt, p.dx, p.dy, p.g, (const T*)c->eta[a], (const T*)c->u[a], (const T*)c->v[a], (const T*)c->z,
         (const T*)c->n2, (const T*)c->ps[0], (const T*)c->ps[1], (const T*)c->ps[2], (T*)c->eta[b], (T*)c->u[b],
         (T*)c->v[b], slot_next, area);
     return cudaGetLastError();

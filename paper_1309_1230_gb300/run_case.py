@@ -5,9 +5,12 @@ Used for profiler captures and quick throughput checks, e.g.
     python -m paper_1309_1230_gb300.run_case --case river --n 4096 --steps 4
     python -m paper_1309_1230_gb300.run_case --case dambreak --n 2048 --precision fp64 --kernel plain
     python -m paper_1309_1230_gb300.run_case --case ensemble --count 64 --steps 100
+    python -m paper_1309_1230_gb300.run_case --case adjoint --n 512 --steps 20 --precision fp32
 
 (the ensemble case runs the batched FP32 form: --count dam breaks with sides
-U{128..min(n, 1024)}, all --steps in one persistent launch)
+U{128..min(n, 1024)}, all --steps in one persistent launch; the adjoint case
+runs swe_adjoint over --steps steps on the n x n adjoint workload, synthetic
+gauge records, and prints its wall time)
 
 Prints one line with the step time measured with CUDA events.
 """
@@ -20,7 +23,7 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="river", choices=["river", "dambreak", "basin", "ensemble"])
+    ap.add_argument("--case", default="river", choices=["river", "dambreak", "basin", "ensemble", "adjoint"])
     ap.add_argument("--count", type=int, default=256, help="ensemble: number of scenarios")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=4)
@@ -42,6 +45,8 @@ def main(argv=None):
 
     if a.case == "ensemble":
         return run_ensemble(a)
+    if a.case == "adjoint":
+        return run_adjoint(a)
     if a.case == "river":
         case = I.river(a.n, a.n)
     elif a.case == "dambreak":
@@ -101,6 +106,30 @@ def run_ensemble(a):
     print(json.dumps({"case": "ensemble", "count": a.count, "cells": cells, "steps": a.steps, "dry_skip": a.dry_skip,
                       "ms_per_call": ms, "cell_updates_per_s": cells * a.steps / (ms / 1e3), "time": time.time()}))
     b.close()
+
+
+def run_adjoint(a):
+    import numpy as np
+    import torch
+
+    from . import inputs as I
+    from . import swe
+
+    c = I.adjoint_case(a.n, a.n)
+    prec = swe.SWE_FP32 if a.precision == "fp32" else swe.SWE_FP64
+    rng = np.random.Generator(np.random.PCG64(5))
+    obs = c["eta"].ravel()[c["gauges"]][None, :] + 0.01 * rng.standard_normal((a.steps, len(c["gauges"])))
+    s = swe.Solver(a.n, a.n, manning_n=0.03, kappa=0.0, precision=prec)
+    s.set_bed(c["z"], np.full((a.n, a.n), 0.03))
+    s.set_state(c["eta"], c["u"], c["v"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, gn, ge, gz = s.adjoint(a.steps, c["gauges"], obs, with_bed=True)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    print(json.dumps({"case": "adjoint", "n": a.n, "precision": a.precision, "steps": a.steps, "seconds": secs,
+                      "loss": loss, "time": time.time()}))
+    s.close()
 
 
 if __name__ == "__main__":
