@@ -130,6 +130,8 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
         const __grid_constant__ CUtensorMap zz, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[fz::NSLOT];
+    __shared__ double sh_tot[6];      // fz::Acc of the current item
+    __shared__ T sh_side[4][32];      // fz::ItemAcc::side
     const int lane = threadIdx.x & 31;
     if (lane == 0)
         for (int q = 0; q < fz::NSLOT; ++q) fz::mbar_init(&bars[q], 1);
@@ -204,8 +206,19 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
             io.u1 = B.planes[1 - cur][1] + off;
             io.v1 = B.planes[1 - cur][2] + off;
             io.n2 = nullptr;
-            const double dt = scen_dt(B, bi.s, k);
-            const StepK<T> S = make_stepk<T>(dt, B.dx, B.dy, B.g);
+            // the scenario's step size and constants: FP64 divisions in one lane, then broadcast
+            double dt = 0.0;
+            StepK<T> S;
+            if (lane == 0) {
+                dt = scen_dt(B, bi.s, k);
+                S = make_stepk<T>(dt, B.dx, B.dy, B.g);
+            }
+            dt = __shfl_sync(0xffffffffu, dt, 0);
+            S.dt = __shfl_sync(0xffffffffu, S.dt, 0);
+            S.dtdx = __shfl_sync(0xffffffffu, S.dtdx, 0);
+            S.dtdy = __shfl_sync(0xffffffffu, S.dtdy, 0);
+            S.g_dtdx = __shfl_sync(0xffffffffu, S.g_dtdx, 0);
+            S.g_dtdy = __shfl_sync(0xffffffffu, S.g_dtdy, 0);
             const int x0 = bi.kx * Gm::OUT;
             I.xw = sx > 0 ? x0 - CPT : x0;
             I.xb = (I.xw - 2) & ~(Gm::ALIGN - 1);
@@ -218,18 +231,19 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
             I.out_lane = sx > 0 ? lane != 0 : lane != 31;
             I.edge = (I.xw - 2 < 0) || (I.xw + Gm::W + 1 > sc.nx - 1);
             Acc acc;
-            acc.clamp = acc.bw = acc.be = acc.bs = acc.bn = acc.smax = 0.0;
+            acc.p = sh_tot;
+            if (lane < 6) acc.p[lane] = 0.0;
+            __syncwarp();
             acc.bad = false;
-            if (sx > 0) fz::run_item<T, CPT, 1, 1, KAPPA>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out);
-            else fz::run_item<T, CPT, -1, -1, KAPPA>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out);
+            bool all_wet;
+            if (sx > 0) fz::run_item<T, CPT, 1, 1, KAPPA, false>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out, false, all_wet, &sh_side[0][lane]);
+            else fz::run_item<T, CPT, -1, -1, KAPPA, false>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out, false, all_wet, &sh_side[0][lane]);
             // per-scenario reductions of this item
-            double v[6] = {acc.smax, acc.clamp, acc.bw, acc.be, acc.bs, acc.bn};
+            // the item's totals, reduced over the warp by run_item
+            __syncwarp();
+            double v[6];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-#pragma unroll
-                for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
-            }
+            for (int m = 0; m < 6; ++m) v[m] = acc.p[m];
             const bool bad = __any_sync(0xffffffffu, acc.bad);
             if (lane == 0) {
                 DevCtl* c = &B.ctl[bi.s];

@@ -334,10 +334,18 @@ __device__ __forceinline__ vecn<T, N> tmax(vecn<T, N> a, vecn<T, N> b) {
     return r;
 }
 
+// The WET forms below serve stencils whose every cell is known to be wet (h
+// > h_dry) in the state they read and, where they clamp, in the state they
+// produce: each wet/dry select then picks the value the arithmetic computes,
+// so they return that value and round exactly like the general form.  The
+// caller checks the wetness and recomputes with the general form where it
+// fails.
+
 // Elevation of neighbour nb seen by the pressure term of a cell at elevation
 // eta_self: a dry neighbour whose bed is above eta_self acts as a wall.
-template <class R, class T>
+template <bool WET = false, class R, class T>
 __device__ __forceinline__ R eta_seen(const Cell<R>& nb, R eta_self, T h_dry) {
+    if constexpr (WET) return nb.e;
     const auto dry = !((nb.e - nb.z) > R(h_dry));
     return sel(dry && (nb.z > eta_self), eta_self, nb.e);
 }
@@ -382,11 +390,12 @@ __device__ __forceinline__ void faces(T qc, T qn, bool lo, bool hi, int side_lo,
 }
 
 // Manning coefficient of a cell (S6/S12): g n^2 |U| / h^(4/3) when wet.
-template <class R, class T>
+template <bool WET = false, class R, class T>
 __device__ __forceinline__ R friction(const Cell<R>& c, R gn2, T h_dry) {
     const R h = c.e - c.z;
     const R s2 = fma_(c.u, c.u, c.v * c.v);  // >= +0, and sqrt(+0) = +0
     const R mag = rsq_sqrt(s2);
+    if constexpr (WET) return gn2 * mag * pow_m43(h);
     return sel(h > R(h_dry), gn2 * mag * pow_m43(h), R(0));
 }
 
@@ -406,11 +415,11 @@ __device__ __forceinline__ R continuity(R e0, R fe, R fw, R fn, R fs, const Step
 // gradient from the one-sided differences in directions DX/DY, with the
 // point-implicit friction of coefficient cf (FR = 1: explicit friction,
 // vel0 - dt A - dt cf vel, the ablation form).
-template <int DX, int DY, int FR = 0, class R, class T>
+template <int DX, int DY, int FR = 0, bool WET = false, class R, class T>
 __device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn, R cf, R u0, R v0,
                                          const StepK<T>& S, T h_dry, R& uo, R& vo) {
-    const R ex = eta_seen(xn, c.e, h_dry);
-    const R ey = eta_seen(yn, c.e, h_dry);
+    const R ex = eta_seen<WET>(xn, c.e, h_dry);
+    const R ey = eta_seen<WET>(yn, c.e, h_dry);
     R dux, dvx, dex, duy, dvy, dey;
     if (DX > 0) { dux = xn.u - c.u; dvx = xn.v - c.v; dex = ex - c.e; }
     else        { dux = c.u - xn.u; dvx = c.v - xn.v; dex = c.e - ex; }
@@ -429,13 +438,13 @@ __device__ __forceinline__ void momentum(const Cell<R>& c, const Cell<R>& xn, co
     vo = smul(v0 - av, r);
 }
 
-template <int DX, int DY, int FR = 0, class R, class T>
+template <int DX, int DY, int FR = 0, bool WET = false, class R, class T>
 __device__ __forceinline__ void stage(const Cell<R>& c, const Cell<R>& xn, const Cell<R>& yn,
                                       R fe, R fw, R fn, R fs, R e0, R u0, R v0, R gn2,
                                       const StepK<T>& S, T h_dry, R& eo, R& uo, R& vo) {
     eo = continuity(e0, fe, fw, fn, fs, S);
-    const R cf = friction(c, gn2, h_dry);
-    momentum<DX, DY, FR>(c, xn, yn, cf, u0, v0, S, h_dry, uo, vo);
+    const R cf = friction<WET>(c, gn2, h_dry);
+    momentum<DX, DY, FR, WET>(c, xn, yn, cf, u0, v0, S, h_dry, uo, vo);
 }
 
 // Wet/dry fix (S8/S16): negative depth -> eta = z (returns the added depth),
@@ -477,6 +486,11 @@ template <class M, class R>
 __device__ __forceinline__ R face_eps(M wet_a, M wet_b, R nu_a, R nu_b) {
     return sel(wet_a && wet_b, tmax(nu_a, nu_b), R(0.0f));
 }
+// The same between two cells known to be wet.
+template <class R>
+__device__ __forceinline__ R face_eps_wet(R nu_a, R nu_b) {
+    return tmax(nu_a, nu_b);
+}
 
 // S15 dissipation flux through one face: eps * (phi_above - phi_below).
 template <class T>
@@ -493,20 +507,20 @@ __device__ __forceinline__ R dissip_faces(R out, R fe, R fw, R fn, R fs, T kappa
 }
 
 // CFL speed of a cell (S2); 0 for dry cells.
-template <class T>
+template <bool WET = false, class T>
 __device__ __forceinline__ T cfl_speed(T e, T u, T v, T z, const GridK<T>& G) {
     T h = e - z;
-    if (!(h > G.h_dry)) return T(0);
+    if (!WET && !(h > G.h_dry)) return T(0);
     T c = rsq_sqrt(G.g * h);
     return fma_(fabs(u) + c, G.inv_dx, (fabs(v) + c) * G.inv_dy);
 }
 
-template <class T, int N>
+template <bool WET = false, class T, int N>
 __device__ __forceinline__ vecn<T, N> cfl_speed(vecn<T, N> e, vecn<T, N> u, vecn<T, N> v, vecn<T, N> z,
                                                 const GridK<T>& G) {
     vecn<T, N> r;
 #pragma unroll
-    for (int i = 0; i < N; ++i) r[i] = cfl_speed(e[i], u[i], v[i], z[i], G);
+    for (int i = 0; i < N; ++i) r[i] = cfl_speed<WET>(e[i], u[i], v[i], z[i], G);
     return r;
 }
 

@@ -90,27 +90,30 @@ cudaError_t swe_fused_prepare(swe_ctx* c) {
         memset(c->tmaps, 0, sizeof(Plan));
     }
     Plan& pl = *(Plan*)c->tmaps;
-    if (c->real_size == 4) return prepare_t<float, 2>(c, pl);
+    if (c->real_size == 4) return prepare_t<float, CPT_F32>(c, pl);
     return prepare_t<double, 2>(c, pl);
 }
 
 // Candidate rows per item for the autotuner: the heights that give about q
-// items per resident warp for q in {1, 2, 3, 4, 6, 8}, and 32 and 64 rows;
-// multiples of 4 in [16, 512], ascending, no repeats.
+// items per resident warp for q in {1, 2, 3, 4, 5, 6, 8}, and 16, 32, 64, 96
+// and 128 rows; multiples of 4 in [16, 512], ascending, no repeats.
 int swe_fused_row_candidates(swe_ctx* c, int* out, int cap) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->p.device);
     const int per_sm = c->real_size == 4 ? occupancy_f32(c) : occupancy_f64(c);
     const double warps = (double)sms * per_sm * NWARP;
-    const int nxs = (c->p.nx + Geo<float, 2>::OUT - 1) / Geo<float, 2>::OUT;
-    int v[8], n = 0;
-    const int q[6] = {1, 2, 3, 4, 6, 8};
-    for (int i = 0; i < 6; ++i) {
+    const int nxs = (c->p.nx + Geo<float, CPT_F32>::OUT - 1) / Geo<float, CPT_F32>::OUT;
+    int v[12], n = 0;
+    const int q[7] = {1, 2, 3, 4, 5, 6, 8};
+    for (int i = 0; i < 7; ++i) {
         int L = ((int)std::ceil((double)c->p.ny * nxs / (q[i] * warps)) + 3) / 4 * 4;
         v[n++] = L < 16 ? 16 : (L > 512 ? 512 : L);
     }
+    v[n++] = 16;
     v[n++] = 32;
     v[n++] = 64;
+    v[n++] = 96;
+    v[n++] = 128;
     std::sort(v, v + n);
     const int m = (int)(std::unique(v, v + n) - v);
     for (int i = 0; i < m && i < cap; ++i) out[i] = v[i];

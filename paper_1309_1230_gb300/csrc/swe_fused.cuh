@@ -50,6 +50,8 @@ constexpr int NWARP = 1;           // warps per CTA (one: item and row branches 
 constexpr int NSLOT = 8;           // ring slots per warp (a power of two)
 constexpr int NPRE = NSLOT - 4;    // rows loaded ahead of the current row
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // cycles (~2 s) before a wait gives up
+constexpr int CPT_F32 = 2;         // cells per lane of the FP32 form (FP64: 2)
+constexpr unsigned WET_SHARE = 50; // see sh_wet in k_fused
 
 template <class T, int CPT>
 struct Geo {
@@ -84,10 +86,13 @@ struct Args : ItemIO<T> {
     int slot_cur, slot_next, slot_zero;
     int nxs, nys, L, nitems;
     int nfull;                     // row bands of the full L rows
-    // dry-item skip (null: off): per item, bit 0 = no wet output cell, bit 1 =
-    // both ping-pong copies of the item agree; written for level k+1 in step k
+    // per-item flags, written for level k+1 in step k: bit 0 = no wet output
+    // cell, bit 1 = both ping-pong copies of the item agree (both for the
+    // dry-item skip), bit 2 = some output cell not known to be wet (the
+    // all-wet pass is not tried next to it); null: none
     const unsigned* fl_in;
     unsigned* fl_out;
+    bool skip;                     // dry-item skip
     int inflow_mask;               // bit s: side s has an inflow boundary
 };
 
@@ -199,15 +204,19 @@ struct Carry {
     Vec<T, CPT> DX[2][3];
 };
 
-struct Acc {  // per-warp totals over its items, FP64
-    double clamp, bw, be, bs, bn, smax;
+// Totals that change once per item (the warp's FP64 totals) or only in
+// boundary rows (an item's side tallies, one slot per lane at stride 32) sit
+// in shared memory, so that they hold no registers through the row loop.
+struct Acc {  // per-warp totals over its items, FP64: p[m], m = 0 smax, 1 clamp, 2..5 sides W, E, S, N
+    double* p;
     bool bad;
 };
 
 template <class T>
 struct ItemAcc {  // per-item totals in the state's real type
-    T clamp, bw, be, bs, bn, smax;
+    T clamp, smax;
     bool bad;
+    T* side;      // side[q * 32]: boundary inflow through side q = W, E, S, N
 };
 
 template <class T, int CPT>
@@ -323,12 +332,29 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 // dissipation and fix of row C = r-2 (S1-S16).  PAR is k's parity.  The
 // arithmetic works on the lane's CPT cells at once (Vec); boundary cases
 // patch single cells.  NF (lean rows): 1 when a per-cell Manning field is
-// set, so that a lean row has no branch on it.
-template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int NF>
+// set, so that a lean row has no branch on it.  WET (lean rows; `wet` in the
+// general ones): the item runs on the assumption that every cell it reads or
+// produces is wet; a lean row then leaves out every wet/dry select (the WET
+// forms of swe_cell.cuh), and every row checks the assumption into `ok` (the
+// level-n row entering the window, the ring's halo cells a lean row reads,
+// the predicted and the new cells), so that the caller recomputes the item
+// without it where it fails.  Without it, `ok` collects whether every new
+// cell the item outputs is wet (the hint for the next step).
+template <class M>
+__device__ __forceinline__ bool all_of(const M& m) {
+    bool r = true;
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(m.c) / sizeof(m.c[0])); ++i) r = r && m.c[i];
+    return r;
+}
+
+template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int NF, bool WET>
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
-                                         bool& timed_out) {
+                                         bool& timed_out, bool& ok, bool wet) {
+    constexpr bool WA = WET && !GEN;  // wet arithmetic: the lean row without selects
+    const bool ck = GEN ? wet : WET;  // check the all-wet assumption
     using V = Vec<T, CPT>;
     constexpr int CX = -SX, CY = -SY;
     constexpr int Q = PAR, O = 1 - PAR;  // this row's buffers, the previous row's
@@ -371,6 +397,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         if (r - 2 < 0) ghost_row(R2, SIDE_S, G); else if (r - 2 >= ny) ghost_row(R2, SIDE_N, G);
     }
     const V h0 = R0.e - R0.z, h1 = R1.e - R1.z, h2 = R2.e - R2.z;
+    if (ck) ok = ok && all_of(h0 > hdv);  // each level-n row of the window enters once as row r
 
     // -------- y switch of row r-1, y dissipation flux through the face between
     // rows r-2 and r-1 (north face of the corrector's row, south face of the predictor's)
@@ -378,7 +405,9 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     if (KAPPA) {
         const bool face_in = !brow || (r - 2 >= 0 && r - 1 < ny);
         const V nyn = nu_switch(h2, h1, h0);
-        V eps = face_eps(h2 > hdv, h1 > hdv, Cy.NY[O], nyn);
+        V eps;
+        if (WA) eps = face_eps_wet(Cy.NY[O], nyn);
+        else eps = face_eps(h2 > hdv, h1 > hdv, Cy.NY[O], nyn);
         if (!face_in) eps = V(T(0));
         FYQ[0] = dflux(eps, R1.e, R2.e);
         FYQ[1] = dflux(eps, R1.u, R2.u);
@@ -406,8 +435,10 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             xn.e[j] = q.e; xn.u[j] = q.u; xn.v[j] = q.v; xn.z[j] = q.z;
         }
         const V qx = h1 * c.u, qy = h1 * c.v;
-        const V qxn = (xn.e - xn.z) * xn.u;
+        const V hxn = xn.e - xn.z;
+        const V qxn = hxn * xn.u;
         const V qyn = hyn * yn.v;
+        if (WA) ok = ok && hxn[SX > 0 ? CPT - 1 : 0] > hd;  // the ring's halo cell
         V fe, fw, fn, fs;
         if (SX > 0) { fe = qxn; fw = qx; } else { fe = qx; fw = qxn; }
         if (SY > 0) { fn = qyn; fs = qy; } else { fn = qy; fs = qyn; }
@@ -444,22 +475,25 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         }
         PR<T, CPT>& P = Cy.P[Q];
         V eo, uo, vo;
-        stage<SX, SY>(cells(c), cells(xn), cells(yn), fe, fw, fn, fs, c.e, c.u, c.v, gn2v, S, hd, eo, uo, vo);
-        V ad = wetdry_fix(eo, uo, vo, c.z, hd);
-        if (edge) {
+        stage<SX, SY, 0, WA>(cells(c), cells(xn), cells(yn), fe, fw, fn, fs, c.e, c.u, c.v, gn2v, S, hd, eo, uo, vo);
+        if (!WA) {
+            V ad = wetdry_fix(eo, uo, vo, c.z, hd);
+            if (edge) {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j)
-                if (I.x0c + j >= nx) ad[j] = T(0);
+                for (int j = 0; j < CPT; ++j)
+                    if (I.x0c + j >= nx) ad[j] = T(0);
+            }
+            T added = T(0);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) added += ad[j];
+            // a predicted clamp counts once per cell: in the item and lane that output it
+            if (I.st_lane && p >= I.plo && p < I.phi)
+                ia.clamp = fma_(T(0.5), added, ia.clamp);
         }
-        T added = T(0);
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) added += ad[j];
         P.e = eo; P.u = uo; P.v = vo; P.z = c.z;
-        P.qy = (eo - c.z) * vo;
-        // a predicted clamp counts once per cell: in the item and lane that output it
-        if (I.st_lane && p >= I.plo && p < I.phi)
-            ia.clamp = fma_(T(0.5), added, ia.clamp);
-
+        const V hp = eo - c.z;
+        P.qy = hp * vo;
+        if (ck && (!GEN || (p >= 0 && p < ny))) ok = ok && all_of(hp > hdv);  // every lane's predicted cells feed a corrector
         if (KAPPA) {
             // x dissipation of row r-1; the outer neighbour on the other side
             // from the ring as well
@@ -472,6 +506,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             const Row<T, CPT>& L = SX > 0 ? xo : xn;  // left neighbours
             const Row<T, CPT>& Rr = SX > 0 ? xn : xo; // right neighbours
             V hl = L.e - L.z, hr = Rr.e - Rr.z;
+            if (WA) ok = ok && (SX > 0 ? hl[0] : hr[CPT - 1]) > hd;  // the ring's other halo cell
             if (edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
@@ -501,7 +536,9 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
 #pragma unroll
             for (int j = 0; j + 1 < CPT; ++j) nur[j] = nuc[j + 1];
             nur[CPT - 1] = nu_hi;
-            V eps = face_eps(h1 > hdv, hr > hdv, nuc, nur);
+            V eps;
+            if (WA) eps = face_eps_wet(nuc, nur);
+            else eps = face_eps(h1 > hdv, hr > hdv, nuc, nur);
             if (edge) {
 #pragma unroll
                 for (int j = 0; j < CPT; ++j)
@@ -509,7 +546,9 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             }
             const V fr[3] = {dflux(eps, Rr.e, c.e), dflux(eps, Rr.u, c.u), dflux(eps, Rr.v, c.v)};
             // west face of the first cell; the others' west faces are their left neighbours' east faces
-            T e0 = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
+            T e0;
+            if (WA) e0 = face_eps_wet(nu_lo, nuc[0]);
+            else e0 = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
             if (edge && I.x0c - 1 < 0) e0 = T(0);
             const T fl0[3] = {dflux(e0, c.e[0], L.e[0]), dflux(e0, c.u[0], L.u[0]), dflux(e0, c.v[0], L.v[0])};
 #pragma unroll
@@ -582,7 +621,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         Cell<V> cy;
         cy.e = ys.e; cy.u = ys.u; cy.v = ys.v; cy.z = ys.z;
         V eo, uo, vo;
-        stage<CX, CY>(cells(cs), cells(xs), cy, fe, fw, fn, fs, R2.e, R2.u, R2.v, gn2v, S, hd, eo, uo, vo);
+        stage<CX, CY, 0, WA>(cells(cs), cells(xs), cy, fe, fw, fn, fs, R2.e, R2.u, R2.v, gn2v, S, hd, eo, uo, vo);
         const V half(T(0.5));
         V oe = half * (cs.e + eo);
         V ou = half * (cs.u + uo);
@@ -594,8 +633,20 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             ou = fma_(kap, Cy.DX[O][1] + FYQ[1], ou);
             ov = fma_(kap, Cy.DX[O][2] + FYQ[2], ov);
         }
-        V ad = wetdry_fix(oe, ou, ov, cs.z, hd);
-        V spj = cfl_speed(oe, ou, ov, cs.z, G);
+        // a lean row of an item's first pair (k < 4) runs the corrector on rows
+        // of the item above: nothing of it is stored or tallied
+        const bool st = I.st_lane && (GEN || k >= 4);
+        // the new cells the item outputs are wet (the fix below keeps a cell
+        // whose depth is above h_dry as it is)
+        const V hn = oe - cs.z;
+        bool wn = true;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) wn = wn && ((edge && I.x0c + j >= nx) || hn[j] > hd);
+        ok = ok && (!st || wn);
+        V ad;
+        if (WA) ad = V(T(0));
+        else ad = wetdry_fix(oe, ou, ov, cs.z, hd);
+        V spj = cfl_speed<WA>(oe, ou, ov, cs.z, G);
         const V sum = oe + ou + ov;
         const V dsum = sum - sum;  // NaN for a non-finite cell
         if (edge) {
@@ -611,7 +662,6 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             sp = spj[j] > sp ? spj[j] : sp;
             bad = bad || !(dsum[j] == T(0));
         }
-        const bool st = I.st_lane;
         const bool own = st && C >= G.own_lo && C < G.own_hi;  // halo rows of a strip: stored, not tallied
         ia.clamp += own ? added : T(0);
         ia.smax = (own && sp > ia.smax) ? sp : ia.smax;
@@ -635,8 +685,8 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 const T qxn0 = h2[j] * R2.u[j];
                 const T w = T(0.5) * (face_bnd(SIDE_W, qxn0, G) + face_bnd(SIDE_W, qx[j], G));
                 const T e = T(0.5) * (face_bnd(SIDE_E, qxn0, G) + face_bnd(SIDE_E, qx[j], G));
-                ia.bw += (own && I.x0c + j == 0) ? w : T(0);
-                ia.be -= (own && I.x0c + j == nx - 1) ? e : T(0);
+                ia.side[0] += (own && I.x0c + j == 0) ? w : T(0);
+                ia.side[32] -= (own && I.x0c + j == nx - 1) ? e : T(0);
             }
         }
         if (brow && (C == 0 || C == ny - 1)) {
@@ -646,8 +696,8 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 const T qyn = h2[j] * R2.v[j];
                 const T sv = T(0.5) * (face_bnd(SIDE_S, qyn, G) + face_bnd(SIDE_S, pc.qy[j], G));
                 const T nv = T(0.5) * (face_bnd(SIDE_N, qyn, G) + face_bnd(SIDE_N, pc.qy[j], G));
-                ia.bs += (in && C == 0) ? sv : T(0);
-                ia.bn -= (in && C == ny - 1) ? nv : T(0);
+                ia.side[64] += (in && C == 0) ? sv : T(0);
+                ia.side[96] -= (in && C == ny - 1) ? nv : T(0);
             }
         }
     };
@@ -659,116 +709,147 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         predictor();
         if (!GEN || k >= 4) corrector();
     }
-    __syncwarp();
+    // the ring slot refilled next was read two rows ago: lean rows come in pairs
+    // and sync after the second
+    if (GEN || PAR == 1) __syncwarp();
 }
 
-// Returns (for the whole warp) whether any output cell of the item is wet.
-template <class T, int CPT, int SX, int SY, bool KAPPA>
-__device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
-                                         Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
-                                         const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out) {
-    I.st_lane = I.out_lane && I.x0c >= 0 && I.x0c < A.G.nx;
-    I.plo = max(I.y0, A.G.own_lo);
-    I.phi = min(I.y1, A.G.own_hi);
-    fence_async_smem();  // the previous item's rows were read through the generic proxy
+// The rows of one item.  wet (only with TRY_WET): on the assumption that
+// every cell is wet (row_step).  Returns 2 (for the whole warp) when that
+// assumption failed, as soon as a pair of rows or the item shows it, with the
+// pass's loads drained; else 0 when every new cell the item outputs is wet,
+// 1 when not.  I.g0 has moved past the pass's loads either way.
+template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
+__device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, ItemCtx<T, CPT>& I,
+                                        Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
+                                        const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
+                                        bool& timed_out, bool wet) {
+    wet = TRY_WET && wet;
+    fence_async_smem();  // the previous pass's rows were read through the generic proxy
 #pragma unroll
     for (int k = 0; k < NPRE; ++k)
         if (k < I.nr) issue_row<T, CPT>(I, k, tme, tmu, tmv, tmz);
     Cy.NY[0] = Cy.NY[1] = Vec<T, CPT>(T(0));
 #pragma unroll
     for (int f = 0; f < 3; ++f) Cy.DX[0][f] = Cy.DX[1][f] = Vec<T, CPT>(T(0));
-    ItemAcc<T> ia;
-    ia.clamp = ia.bw = ia.be = ia.bs = ia.bn = ia.smax = T(0);
+    ia.clamp = ia.smax = T(0);
     ia.bad = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ia.side[q * 32] = T(0);
+    bool ok = true, held = true;
+    const int nr = I.nr;
+    int drain_from = 0, issued = 0;  // after a failed wait or check: the rows to drain, [drain_from, issued)
     int k = 0;
-    int kf = 0;  // after a failed wait: the last row whose loads may have been issued is kf + NPRE
     const int ny = A.G.ny;
 #pragma unroll 1
-    for (; k + 1 < I.nr; k += 2) {
+    for (; k < nr; k += 2) {
         const int r = I.y0 - 2 + k;
-        if (!I.edge && k >= 4 && r - 2 > 0 && r + 1 < ny) {
+        // lean rows from the item's second pair on (the first, k = 0 and 1, only
+        // loads), away from the boundaries
+        if (!I.edge && k >= 2 && k + 1 < nr && r - 2 > 0 && r + 1 < ny) {
             // both rows' loads and waits first, so that the two rows schedule as
             // one block; the slots refilled were last read in the previous pair
             fence_async_smem();
-            if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
-            if (k + 1 + NPRE < I.nr) issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz);
-            if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) { timed_out = true; kf = k + 1; break; }
-            if (A.n2 != nullptr) {
-                row_step<T, CPT, SX, SY, KAPPA, 0, false, 1>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-                row_step<T, CPT, SX, SY, KAPPA, 1, false, 1>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            } else {
-                row_step<T, CPT, SX, SY, KAPPA, 0, false, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-                row_step<T, CPT, SX, SY, KAPPA, 1, false, 0>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
+            if (k + NPRE < nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
+            if (k + 1 + NPRE < nr) issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz);
+            if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) {
+                timed_out = true; drain_from = k; issued = min(nr, k + 2 + NPRE); break;
             }
+#define SWE_PAIR(NF, W)                                                                                           \
+    row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);     \
+    row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
+            if (TRY_WET && wet) {
+                if (A.n2 != nullptr) { SWE_PAIR(1, TRY_WET); } else { SWE_PAIR(0, TRY_WET); }
+            } else {
+                if (A.n2 != nullptr) { SWE_PAIR(1, false); } else { SWE_PAIR(0, false); }
+            }
+#undef SWE_PAIR
         } else {
-            row_step<T, CPT, SX, SY, KAPPA, 0, true, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            if (timed_out) { kf = k; break; }
-            row_step<T, CPT, SX, SY, KAPPA, 1, true, 0>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-            if (timed_out) { kf = k + 1; break; }
+            row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);
+            if (timed_out) { drain_from = k; issued = min(nr, k + 1 + NPRE); break; }
+            if (k + 1 < nr) {  // the last row of an odd count runs alone
+                row_step<T, CPT, SX, SY, KAPPA, 1, true, 0, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out,
+                                                                   ok, wet);
+                if (timed_out) { drain_from = k + 1; issued = min(nr, k + 2 + NPRE); break; }
+            }
+        }
+        if (TRY_WET && wet && !__all_sync(FULL, ok)) {
+            held = false; drain_from = min(nr, k + 2); issued = min(nr, k + 2 + NPRE); break;
         }
     }
-    if (!timed_out && k < I.nr) {
-        row_step<T, CPT, SX, SY, KAPPA, 0, true, 0>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out);
-        kf = k;
-    }
-    if (timed_out) {
-        // drain this item's loads still in flight (bounded) before the ring is reused or left
-        const int issued = I.nr < kf + NPRE + 1 ? I.nr : kf + NPRE + 1;
-        for (int q = k; q < issued; ++q) {
+    const bool all_ok = held && __all_sync(FULL, ok);
+    if (TRY_WET && wet && held && !timed_out && !all_ok) { held = false; drain_from = nr; issued = nr; }
+    if (timed_out || !held) {
+        // drain this pass's loads still in flight (bounded) before the ring is reused or left
+        for (int q = drain_from; q < issued; ++q) {
             const unsigned g = I.g0 + (unsigned)q;
             unsigned long long t0 = clock64();
             while (!mbar_try(I.bars + (g & (NSLOT - 1)), (g / NSLOT) & 1u))
                 if (clock64() - t0 > WAIT_LIMIT / 8) break;
         }
+        I.g0 += (unsigned)issued;
+        __syncwarp();
+        return held ? 1 : 2;
     }
-    I.g0 += (unsigned)I.nr;
-    acc.clamp += (double)ia.clamp;
-    acc.bw += (double)ia.bw; acc.be += (double)ia.be; acc.bs += (double)ia.bs; acc.bn += (double)ia.bn;
-    acc.smax = fmax(acc.smax, (double)ia.smax);
-    acc.bad = acc.bad || ia.bad;
-    return __any_sync(FULL, ia.smax > T(0));
+    I.g0 += (unsigned)nr;
+    return all_ok ? 0 : 1;
 }
 
-template <class T, int CPT, int SX, int SY, bool KAPPA>
-__global__ void __launch_bounds__(NWARP * 32, Geo<T, CPT>::MINB)
-k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtensorMap tmu,
-        const __grid_constant__ CUtensorMap tmv, const __grid_constant__ CUtensorMap tmz, const Args<T> A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[NWARP][NSLOT];
-    __shared__ double sh_dt;
-    __shared__ double red[NWARP][6];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        double dt = A.dt_fixed ? A.dt_fixed[A.s]
-                               : dt_from_speed(__longlong_as_double((long long)A.ctl->smax[A.slot_cur]), A.cfl, A.dt_max);
-        sh_dt = dt;
-        if (blockIdx.x == 0) {
-            DevCtl* c = A.ctl;
-            c->dt_last = dt;
-            c->t += dt;
-            c->dt_min = fmin(c->dt_min, dt);
-            c->dt_maxs = fmax(c->dt_maxs, dt);
-            A.dt_hist[A.s] = dt;
-            c->smax[A.slot_zero] = 0ull;
-            c->qctr[A.slot_zero] = 0u;  // the previous step's queue (all its CTAs have finished)
-        }
+// Returns (for the whole warp) whether any output cell of the item is wet;
+// all_wet: whether every output cell is.  try_wet: run the item on the
+// all-wet assumption first, and again in the general form where it fails
+// (only when TRY_WET: the FP32 form, where the wet/dry selects are a large
+// share of the row's instructions).  The item's tallies are reduced over the
+// warp in FP64 and added to the warp's totals, acc.p[m] (lane 0 keeps them).
+template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
+__device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
+                                         Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
+                                         const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out,
+                                         bool try_wet, bool& all_wet, T* side) {
+    I.st_lane = I.out_lane && I.x0c >= 0 && I.x0c < A.G.nx;
+    I.plo = max(I.y0, A.G.own_lo);
+    I.phi = min(I.y1, A.G.own_hi);
+    ItemAcc<T> ia;
+    ia.side = side;
+    const bool wet = TRY_WET && try_wet && !I.edge && I.y0 >= A.G.own_lo && I.y1 <= A.G.own_hi;
+    int st = 0;
+    bool w = wet;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {  // one call site: the rows' code is not inlined twice
+        st = run_rows<T, CPT, SX, SY, KAPPA, TRY_WET>(A, S, I, Cy, ia, tme, tmu, tmv, tmz, timed_out, w);
+        if (st != 2 || timed_out) break;
+        w = false;
     }
-    if (lane == 0)
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[warp][s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    __syncthreads();
-    const double dt = sh_dt;
-    const StepK<T> S = make_stepk<T>(dt, A.dx, A.dy, A.g);
+    all_wet = st == 0;
+    double v[6] = {(double)ia.smax, (double)ia.clamp, (double)ia.side[0], (double)ia.side[32], (double)ia.side[64],
+                   (double)ia.side[96]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmax(v[0], __shfl_xor_sync(FULL, v[0], o));
+#pragma unroll
+        for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(FULL, v[m], o);
+    }
+    if (I.lane == 0) {
+        acc.p[0] = fmax(acc.p[0], v[0]);
+#pragma unroll
+        for (int m = 1; m < 6; ++m) acc.p[m] += v[m];
+    }
+    acc.bad = acc.bad || ia.bad;
+    return v[0] > 0.0;
+}
 
-    Acc acc;
-    acc.clamp = acc.bw = acc.be = acc.bs = acc.bn = 0.0;
-    acc.smax = 0.0;
-    acc.bad = false;
-    bool timed_out = false;
+// The work-item loop of one launch.  TRY_WET: items whose neighbourhood was
+// all wet take the all-wet pass (run_item); the loop is compiled once with
+// and once without it, and a launch runs one of the two.  wc: the counts of
+// interior items with and without an all-wet neighbourhood (shared memory).
+template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
+__device__ __forceinline__ void item_loop(const Args<T>& A, const StepK<T>& S, const CUtensorMap* tme,
+                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
+                                          unsigned char* ring, uint64_t* bars, int lane, Acc& acc, bool& timed_out,
+                                          unsigned* wc, T* side) {
     ItemCtx<T, CPT> I;
-    I.ring = smem + warp * Geo<T, CPT>::WARP_SMEM;
-    I.bars = bars[warp];
+    I.ring = ring;
+    I.bars = bars;
     I.lane = lane;
     I.out_lane = SX > 0 ? lane != 0 : lane != 31;
     I.g0 = 0;
@@ -787,20 +868,24 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         int kx, ky;
         item_of(item, A.nxs, A.nfull, kx, ky);
         const int fi = ky * A.nxs + kx;
-        bool dry = false;
+        bool dry = false, try_wet = true;
         if (A.fl_in) {
-            // an item whose 3x3 neighbourhood of items held no wet cell (a radius
-            // of at least 2 cells) keeps its values; if its other copy already
-            // holds them too, the item is skipped
-            dry = !(((A.inflow_mask >> SIDE_W) & 1) && kx == 0) && !(((A.inflow_mask >> SIDE_E) & 1) && kx == A.nxs - 1) &&
+            // lane q < 9 reads the flags of item (kx + q % 3 - 1, ky + q / 3 - 1),
+            // the 3x3 neighbourhood (a radius of at least 2 cells); an item
+            // outside the grid counts as dry and as all wet
+            const int qx = kx + lane % 3 - 1, qy = ky + lane / 3 - 1;
+            const bool in = lane < 9 && qx >= 0 && qy >= 0 && qx < A.nxs && qy < A.nys;
+            const unsigned f = in ? A.fl_in[qy * A.nxs + qx] : 1u;
+            const unsigned fc = __shfl_sync(FULL, f, 4);
+            // an item whose neighbourhood held no wet cell keeps its values; if its
+            // other copy already holds them too, it is skipped
+            dry = A.skip && __all_sync(FULL, f & 1u) &&
+                  !(((A.inflow_mask >> SIDE_W) & 1) && kx == 0) && !(((A.inflow_mask >> SIDE_E) & 1) && kx == A.nxs - 1) &&
                   !(((A.inflow_mask >> SIDE_S) & 1) && ky == 0) && !(((A.inflow_mask >> SIDE_N) & 1) && ky == A.nys - 1);
-            for (int dy = -1; dy <= 1 && dry; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int qx = kx + dx, qy = ky + dy;
-                    if (qx >= 0 && qy >= 0 && qx < A.nxs && qy < A.nys) dry = dry && (A.fl_in[qy * A.nxs + qx] & 1u);
-                }
-            if (dry && (A.fl_in[fi] & 2u)) {
-                if (lane == 0) A.fl_out[fi] = 3u;
+            // a neighbourhood whose every cell was wet is tried on the all-wet assumption
+            try_wet = !__any_sync(FULL, f & 4u);
+            if (dry && (fc & 2u)) {
+                if (lane == 0) A.fl_out[fi] = 7u;
                 item = __shfl_sync(FULL, nxt, 0);
                 continue;
             }
@@ -814,19 +899,88 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         I.y1 = min(A.G.ny, I.y0 + A.L);
         I.nr = I.y1 - I.y0 + 4;
         I.edge = (I.xw - 2 < 0) || (I.xw + Geo<T, CPT>::W + 1 > A.G.nx - 1);
-        const bool wet = run_item<T, CPT, SX, SY, KAPPA>(A, S, acc, I, Cy, &tme, &tmu, &tmv, &tmz, timed_out);
-        if (A.fl_in && lane == 0) A.fl_out[fi] = (wet ? 0u : 1u) | (dry ? 2u : 0u);
+        if (lane == 0 && !I.edge) atomicAdd(&wc[try_wet ? 0 : 1], 1u);
+        bool all_wet;
+        const bool wet = run_item<T, CPT, SX, SY, KAPPA, TRY_WET>(A, S, acc, I, Cy, tme, tmu, tmv, tmz, timed_out,
+                                                                  try_wet, all_wet, side);
+        if (A.fl_in && lane == 0) A.fl_out[fi] = (wet ? 0u : 1u) | (dry ? 2u : 0u) | (all_wet ? 0u : 4u);
         item = __shfl_sync(FULL, nxt, 0);
     }
 
-    // ---- reductions: warp, CTA, then one atomic per CTA
-    double v[6] = {acc.smax, acc.clamp, acc.bw, acc.be, acc.bs, acc.bn};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(FULL, v[0], o));
-#pragma unroll
-        for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(FULL, v[m], o);
+}
+
+template <class T, int CPT, int SX, int SY, bool KAPPA>
+__global__ void __launch_bounds__(NWARP * 32, Geo<T, CPT>::MINB)
+k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtensorMap tmu,
+        const __grid_constant__ CUtensorMap tmv, const __grid_constant__ CUtensorMap tmz, const Args<T> A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[NWARP][NSLOT];
+    __shared__ double sh_dt;
+    __shared__ StepK<T> sh_S;  // the step's constants, divided once per CTA in FP64
+    __shared__ bool sh_wet;    // this step runs the all-wet pass where an item's neighbourhood allows it
+    __shared__ unsigned sh_wc[2];  // the CTA's interior items with and without an all-wet neighbourhood
+    __shared__ double red[NWARP][6];
+    __shared__ double sh_tot[NWARP][6];   // Acc
+    __shared__ T sh_side[NWARP][4][32];   // ItemAcc::side
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        double dt = A.dt_fixed ? A.dt_fixed[A.s]
+                               : dt_from_speed(__longlong_as_double((long long)A.ctl->smax[A.slot_cur]), A.cfl, A.dt_max);
+        sh_dt = dt;
+        sh_S = make_stepk<T>(dt, A.dx, A.dy, A.g);
+        // The all-wet pass and the general lean rows are two large blocks of
+        // code; where both run in one step they contend for the instruction
+        // cache, which costs more than the pass saves.  So the pass runs only
+        // when, in the previous step, the computed interior items that could
+        // not take it were at most 1/WET_SHARE of those that could (every item
+        // can after a reset of the counts).
+        const unsigned* wc = A.ctl->wcnt[A.slot_cur];
+        sh_wet = (unsigned long long)wc[1] * WET_SHARE <= (unsigned long long)wc[0];
+        sh_wc[0] = sh_wc[1] = 0u;
+        if (blockIdx.x == 0) {
+            DevCtl* c = A.ctl;
+            c->dt_last = dt;
+            c->t += dt;
+            c->dt_min = fmin(c->dt_min, dt);
+            c->dt_maxs = fmax(c->dt_maxs, dt);
+            A.dt_hist[A.s] = dt;
+            c->smax[A.slot_zero] = 0ull;
+            c->qctr[A.slot_zero] = 0u;  // the previous step's queue (all its CTAs have finished)
+            c->wcnt[A.slot_zero][0] = c->wcnt[A.slot_zero][1] = 0u;
+        }
     }
+    if (lane == 0)
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[warp][s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    const double dt = sh_dt;
+    const StepK<T> S = sh_S;
+    const bool use_wet = sh_wet;
+
+    Acc acc;
+    acc.p = sh_tot[warp];
+    if (lane < 6) acc.p[lane] = 0.0;
+    __syncwarp();
+    acc.bad = false;
+    bool timed_out = false;
+    if constexpr (sizeof(T) == 4) {
+        if (use_wet)
+            item_loop<T, CPT, SX, SY, KAPPA, true>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
+                                                   bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+        else
+            item_loop<T, CPT, SX, SY, KAPPA, false>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
+                                                    bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+    } else {
+        item_loop<T, CPT, SX, SY, KAPPA, false>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
+                                                bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+    }
+
+    // ---- reductions: warp, CTA, then one atomic per CTA
+    __syncwarp();
+    double v[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) v[m] = acc.p[m];
     const bool bad = __any_sync(FULL, acc.bad);
     const bool tmo = __any_sync(FULL, timed_out);
     if (lane == 0) {
@@ -847,6 +1001,8 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
             unsigned long long* slot = &A.ctl->smax[A.slot_next];
             if (bits > *(volatile unsigned long long*)slot) atomicMax(slot, bits);
         }
+        if (sh_wc[0]) atomicAdd(&A.ctl->wcnt[A.slot_next][0], sh_wc[0]);
+        if (sh_wc[1]) atomicAdd(&A.ctl->wcnt[A.slot_next][1], sh_wc[1]);
         if (t[1] != 0.0) atomicAdd(&A.ctl->clamp, t[1] * A.area);
         if (t[2] != 0.0) atomicAdd(&A.ctl->bflux[0], t[2] * dt * A.dy);
         if (t[3] != 0.0) atomicAdd(&A.ctl->bflux[1], t[3] * dt * A.dy);
@@ -892,7 +1048,8 @@ cudaError_t launch_t(swe_ctx* c, const Plan& pl, int s, long long k) {
     A.slot_cur = (int)(k % 3); A.slot_next = (int)((k + 1) % 3); A.slot_zero = (int)((k + 2) % 3);
     A.nxs = pl.nxs; A.nys = pl.nys; A.L = pl.L; A.nitems = pl.nitems; A.nfull = p.ny / pl.L;
     A.fl_in = nullptr; A.fl_out = nullptr; A.inflow_mask = 0;
-    if (p.dry_skip && pl.flags) {
+    A.skip = p.dry_skip != 0;
+    if (pl.flags) {
         A.fl_in = pl.flags + (size_t)(k & 1) * pl.nitems;
         A.fl_out = pl.flags + (size_t)((k + 1) & 1) * pl.nitems;
         for (int q = 0; q < 4; ++q)

@@ -5,7 +5,7 @@ namespace swe {
 namespace fz {
 
 cudaError_t launch_f32_0(swe_ctx* c, const Plan& pl, int s, long long k) {
-    return launch_dir<float, 2, false>(c, pl, s, k);
+    return launch_dir<float, CPT_F32, false>(c, pl, s, k);
 }
 
 }  // namespace fz

@@ -5,14 +5,14 @@ namespace swe {
 namespace fz {
 
 cudaError_t launch_f32_k(swe_ctx* c, const Plan& pl, int s, long long k) {
-    return launch_dir<float, 2, true>(c, pl, s, k);
+    return launch_dir<float, CPT_F32, true>(c, pl, s, k);
 }
 
 int occupancy_f32(swe_ctx*) {
     int nb = 0;
-    auto kern = k_fused<float, 2, 1, 1, true>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cpt_smem<float, 2>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NWARP * 32, cpt_smem<float, 2>());
+    auto kern = k_fused<float, CPT_F32, 1, 1, true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cpt_smem<float, CPT_F32>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NWARP * 32, cpt_smem<float, CPT_F32>());
     return nb < 1 ? 1 : nb;
 }
 

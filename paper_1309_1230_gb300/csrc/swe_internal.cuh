@@ -20,6 +20,10 @@ struct DevCtl {
     StepSlot cur;                // plain and paper paths: step size and constants of the current step
     unsigned int qctr[3];        // fused path: work-queue counter, slot k%3 = step k
     unsigned int pad2;
+    // fused FP32 path, slot (k+1)%3 = step k's computed interior items whose
+    // neighbourhood was all wet, and those whose neighbourhood was not (step
+    // k+1 runs the all-wet pass only when the second count is small)
+    unsigned int wcnt[3][2];
 };
 
 // Per-call diagnostics reduction result.
@@ -69,7 +73,6 @@ struct swe_ctx {
     uint8_t* seg_wet[2];    // per work item: any wet cell in the level held by buffer b
     uint8_t* seg_same;      // per work item: both buffers hold the same values
     int seg_rows, seg_cols, segs_x, segs_y;
-    int cta_warps;
     void* tmaps;            // device copy of the tensor maps (4 per buffer pair)
     void* paper;            // scratch of the paper-layout step (swe_paper.cu), or NULL
     int own_lo, own_hi;     // own rows of a strip of a decomposed domain (default all rows)

@@ -148,6 +148,7 @@ __global__ void k_call_begin(DevCtl* ctl) {
     ctl->dt_maxs = 0.0;
     ctl->flags = 0u;
     ctl->qctr[0] = ctl->qctr[1] = ctl->qctr[2] = 0u;
+    for (int q = 0; q < 3; ++q) ctl->wcnt[q][0] = ctl->wcnt[q][1] = 0u;
 }
 
 }  // namespace swe

@@ -201,3 +201,23 @@ def open_river(nx: int, ny: int, seed: int = 1315, q_w: float = 2.0, q_s: float 
     c["bc"] = (INFLOW, OUTFLOW, INFLOW, OUTFLOW)
     c["q_in"] = (q_w, 0.0, q_s, 0.0)
     return c
+
+
+def drying_shoals(nx: int = 300, ny: int = 90, depth: float = 0.5, freeboard: float = 0.004,
+                  u0: float = 0.3, q_in: float = 0.15, manning_n: float = 0.03, kappa: float = 0.25) -> dict:
+    """A channel wet everywhere at the start whose shoals dry out as the
+    water flows over them: flat bed with four Gaussian shoals (the highest
+    point `freeboard` below the still surface), uniform depth `depth`, current
+    u0 eastwards, inflow q_in on the west side, free outflow east, walls south
+    and north.  Positions and widths are fixed fractions of the grid."""
+    x, y = _cell_centres(nx, ny)
+    z = np.zeros((ny, nx))
+    for fx, fy, fs in ((0.27, 0.33, 0.13), (0.5, 0.67, 0.11), (0.73, 0.39, 0.16), (0.4, 0.78, 0.09)):
+        cx, cy, s = fx * nx, fy * ny, fs * ny
+        g = np.exp(-((x[None, :] - cx) ** 2 + (y[:, None] - cy) ** 2) / (2.0 * s * s))
+        z = np.maximum(z, (depth - freeboard) * g)
+    eta = np.full((ny, nx), depth)
+    return dict(nx=nx, ny=ny, dx=1.0, dy=1.0, z=z, eta=eta, u=np.full((ny, nx), u0),
+                v=np.zeros((ny, nx)), manning_n=manning_n, kappa=kappa,
+                bc=(INFLOW, OUTFLOW, WALL, WALL), q_in=(q_in, 0.0, 0.0, 0.0))
+

@@ -93,12 +93,41 @@ def test_fused_independent_of_decomposition(name, precision):
     build, steps = CASES[name]
     case = build()
     steps = min(steps, 120)
-    runs = [_run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=L) for L in (0, 16, 37)]
+    runs = [_run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=L) for L in (0, 16, 37, 24)]
     plain = _run(case, precision, swe.SWE_KERNEL_PLAIN, steps)
     for r in runs[1:] + [plain]:
         assert np.array_equal(r[1], runs[0][1])
         for a, b in zip(r[2:], runs[0][2:]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_all_wet_pass_falls_back_where_cells_dry(precision):
+    """The FP32 fused step first runs an item on the assumption that every
+    cell of it is wet, and recomputes it in the general form where a check
+    fails.  A channel wet everywhere at the start, whose shoals then dry,
+    makes items fail the check in mid-run; the state stays bitwise equal to
+    the plain kernel, with and without the per-item flags that steer the
+    pass (the dry-item skip on and off), over one call and several."""
+    from paper_1309_1230_gb300 import swe
+    case = I.drying_shoals(300, 90)
+    steps = 300
+    assert np.min(case["eta"] - case["z"]) > 2e-3
+    plain = _run(case, precision, swe.SWE_KERNEL_PLAIN, steps)
+    h = plain[2] - case["z"]
+    assert 0 < int(np.sum(h <= 1e-3)) < h.size // 10  # the shoals dried
+    for L, skip in ((16, 1), (16, 0), (0, 1)):
+        one = _run(case, precision, swe.SWE_KERNEL_FUSED, steps, seg_rows=L, dry_skip=skip)
+        assert np.array_equal(one[1], plain[1])
+        for a, b in zip(one[2:], plain[2:]):
+            assert np.array_equal(a, b)
+    s = gpu_solver(case, precision, swe.SWE_KERNEL_FUSED, seg_rows=16)
+    d = [s.step(q, want_dt=True)[1] for q in (1, 99, 200)]
+    split = s.get_state()
+    s.close()
+    assert np.array_equal(np.concatenate(d), plain[1])
+    for a, b in zip(split, plain[2:]):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
