@@ -654,18 +654,26 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             for (int j = 0; j < CPT; ++j)
                 if (I.x0c + j >= nx) { ad[j] = T(0); spj[j] = T(0); }
         }
-        T added = T(0), sp = T(0);
-        bool bad = false;
+        // the row's speed maximum (speeds are >= 0 and never NaN in a finite
+        // state; a NaN speed is left out, as the max of fmax does) and the sum of
+        // the cells' NaN probes (0 unless one is NaN)
+        T sp = T(0), dprobe = T(0);
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-            added += ad[j];
-            sp = spj[j] > sp ? spj[j] : sp;
-            bad = bad || !(dsum[j] == T(0));
+            sp = tmax(sp, spj[j]);
+            dprobe += dsum[j];
         }
-        const bool own = st && C >= G.own_lo && C < G.own_hi;  // halo rows of a strip: stored, not tallied
-        ia.clamp += own ? added : T(0);
-        ia.smax = (own && sp > ia.smax) ? sp : ia.smax;
-        ia.bad = ia.bad || (own && bad);
+        // halo rows of a strip are stored, not tallied (the all-wet pass runs
+        // only on items of own rows)
+        const bool own = WA ? st : (st && C >= G.own_lo && C < G.own_hi);
+        if (!WA) {
+            T added = T(0);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) added += ad[j];
+            ia.clamp += own ? added : T(0);
+        }
+        ia.smax = tmax(ia.smax, own ? sp : T(0));
+        ia.bad = ia.bad || (own && !(dprobe == T(0)));
         if constexpr (sizeof(T) == 4 && CPT == 2) {  // predicated stores: no branch in the row
             const size_t o = (size_t)C * G.pitch + I.x0c;
             asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n"
