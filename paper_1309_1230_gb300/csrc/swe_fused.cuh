@@ -287,15 +287,16 @@ __device__ __forceinline__ Cell<Vec<T, CPT>> cells(const Row<T, CPT>& r) {
 }
 
 // Predicated issue of one ring row: lane 0 arms the barrier and starts the
-// four tile loads (no divergent branch).
+// four tile loads, if `want` (no branch).
 template <class T, int CPT>
 __device__ __forceinline__ void issue_row(const ItemCtx<T, CPT>& I, int k, const CUtensorMap* tme,
-                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz) {
+                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
+                                          bool want = true) {
     using Gm = Geo<T, CPT>;
     const unsigned g = I.g0 + (unsigned)k;
     const unsigned bar = saddr(I.bars + (g & (NSLOT - 1)));
     const unsigned dst = saddr(I.ring + (g & (NSLOT - 1)) * Gm::SLOT);
-    const unsigned pred = I.lane == 0 ? 1u : 0u;
+    const unsigned pred = (I.lane == 0 && want) ? 1u : 0u;
     const int y = I.yoff + I.y0 - 2 + k;
     asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}"
                  ::"r"(pred), "r"(bar), "r"(4u * Gm::BW * (unsigned)sizeof(T)) : "memory");
@@ -367,7 +368,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
 
     if (GEN) {  // the lean rows come in pairs, loaded and waited for by the caller
         fence_async_smem();  // ring row k-4 (read two rows ago) is refilled next
-        if (k + NPRE < I.nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
+        issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz, k + NPRE < I.nr);
         if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
     }
     if (GEN && k < 2) return;
@@ -749,28 +750,29 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
     int drain_from = 0, issued = 0;  // after a failed wait or check: the rows to drain, [drain_from, issued)
     int k = 0;
     const int ny = A.G.ny;
+    // Lean rows: pairs from the item's second on (the first, k = 0 and 1, only
+    // loads) whose rows r = y0 - 2 + k and r + 1 keep two rows from the y
+    // sides (r - 2 > 0, r + 1 < ny), in items away from the x sides; with the
+    // all-wet pass compiled in, only for an item that takes it (the others, a
+    // few per launch, run the general rows, so that a launch keeps one lean
+    // loop hot).
+    const int klo = max(2, 5 - I.y0);
+    const int khi = (I.edge || (TRY_WET && !wet)) ? 0 : min(nr - 1, ny - I.y0 + 1);
 #pragma unroll 1
     for (; k < nr; k += 2) {
-        const int r = I.y0 - 2 + k;
-        // lean rows from the item's second pair on (the first, k = 0 and 1, only
-        // loads), away from the boundaries
-        if (!I.edge && k >= 2 && k + 1 < nr && r - 2 > 0 && r + 1 < ny) {
+        if (k >= klo && k < khi) {
             // both rows' loads and waits first, so that the two rows schedule as
             // one block; the slots refilled were last read in the previous pair
             fence_async_smem();
-            if (k + NPRE < nr) issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz);
-            if (k + 1 + NPRE < nr) issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz);
+            issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz, k + NPRE < nr);
+            issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz, k + 1 + NPRE < nr);
             if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) {
                 timed_out = true; drain_from = k; issued = min(nr, k + 2 + NPRE); break;
             }
 #define SWE_PAIR(NF, W)                                                                                           \
     row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);     \
     row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
-            if (TRY_WET && wet) {
-                if (A.n2 != nullptr) { SWE_PAIR(1, TRY_WET); } else { SWE_PAIR(0, TRY_WET); }
-            } else {
-                if (A.n2 != nullptr) { SWE_PAIR(1, false); } else { SWE_PAIR(0, false); }
-            }
+            if (A.n2 != nullptr) { SWE_PAIR(1, TRY_WET); } else { SWE_PAIR(0, TRY_WET); }
 #undef SWE_PAIR
         } else {
             row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);
