@@ -129,12 +129,12 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
         const __grid_constant__ CUtensorMap uB, const __grid_constant__ CUtensorMap vB,
         const __grid_constant__ CUtensorMap zz, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[fz::NSLOT];
+    __shared__ uint64_t bars[fz::NPAIR];
     __shared__ double sh_tot[6];      // fz::Acc of the current item
     __shared__ T sh_side[4][32];      // fz::ItemAcc::side
     const int lane = threadIdx.x & 31;
     if (lane == 0)
-        for (int q = 0; q < fz::NSLOT; ++q) fz::mbar_init(&bars[q], 1);
+        for (int q = 0; q < fz::NPAIR; ++q) fz::mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncwarp();
 
@@ -431,7 +431,7 @@ cudaError_t encode_plane(CUtensorMap* m, void* base, const swe_batch* b) {
     }
     cuuint64_t dims[2] = {(cuuint64_t)b->width, (cuuint64_t)b->rows};
     cuuint64_t strides[1] = {(cuuint64_t)b->pitch * sizeof(T)};
-    cuuint32_t box[2] = {(cuuint32_t)Gm::BW, 1u};
+    cuuint32_t box[2] = {(cuuint32_t)Gm::BW, 2u};  // two rows: one ring slot of the fused row step
     cuuint32_t es[2] = {1u, 1u};
     CUresult r = g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

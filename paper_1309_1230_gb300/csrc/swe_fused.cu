@@ -29,7 +29,7 @@ template <class T, int CPT>
 cudaError_t encode(CUtensorMap* m, const void* base, const swe_ctx* c) {
     cuuint64_t dims[2] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny};
     cuuint64_t strides[1] = {(cuuint64_t)c->pitch * sizeof(T)};
-    cuuint32_t box[2] = {(cuuint32_t)Geo<T, CPT>::BW, 1u};
+    cuuint32_t box[2] = {(cuuint32_t)Geo<T, CPT>::BW, 2u};  // two rows: one ring slot
     cuuint32_t es[2] = {1u, 1u};
     CUresult r = g_encode(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
                           const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

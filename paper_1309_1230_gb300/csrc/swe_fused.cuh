@@ -16,10 +16,9 @@
 // warp loads the segment plus two rows above and below.
 //
 // Data movement.  Level-n rows (eta, u, v, z) stream into a per-warp ring in
-// shared memory with TMA (cp.async.bulk.tensor.2d, completion on an
-// mbarrier), NPRE rows ahead of use; a row stays in the ring while any of the
-// four rows of the step's stencil window still needs it.  Interior rows are
-// loaded and waited for in pairs.  The two predicted rows, the y dissipation
+// shared memory with TMA (cp.async.bulk.tensor.2d, boxes two rows high, one
+// mbarrier per pair of rows), two pairs ahead of use; a row stays in the ring
+// while any of the four rows of the step's stencil window still needs it.  The two predicted rows, the y dissipation
 // switch and the partial dissipation sum the corrector needs are carried in
 // registers from one row to the next.  The level-n x neighbours outside a
 // lane's cells are read from the ring (its columns extend two cells beyond
@@ -47,8 +46,9 @@ namespace fz {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int NWARP = 1;           // warps per CTA (one: item and row branches are then CTA-uniform)
-constexpr int NSLOT = 8;           // ring slots per warp (a power of two)
-constexpr int NPRE = NSLOT - 4;    // rows loaded ahead of the current row
+constexpr int NSLOT = 8;           // ring rows per warp (a power of two): the pair in use, the
+                                   // pair before it (the stencil's rows r-1, r-2) and two pairs in flight
+constexpr int NPAIR = NSLOT / 2;   // ring slots: rows are loaded and waited for in pairs
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;  // cycles (~2 s) before a wait gives up
 constexpr int CPT_F32 = 2;         // cells per lane of the FP32 form (FP64: 2)
 constexpr unsigned WET_SHARE = 50; // see sh_wet in k_fused
@@ -59,9 +59,10 @@ struct Geo {
     static constexpr int OUT = W - CPT;                   // output columns per item
     static constexpr int BW = W + 8;                      // TMA box width (elements)
     static constexpr int ALIGN = 16 / (int)sizeof(T);     // TMA x alignment (elements)
-    static constexpr int FSTRIDE = ((BW * (int)sizeof(T) + 127) / 128) * 128;  // bytes per field row
-    static constexpr int SLOT = 4 * FSTRIDE;              // bytes per ring slot (eta, u, v, z)
-    static constexpr int WARP_SMEM = NSLOT * SLOT;
+    static constexpr int RSTRIDE = BW * (int)sizeof(T);   // bytes of one field row (one TMA box row)
+    static constexpr int FSTRIDE = ((2 * RSTRIDE + 127) / 128) * 128;  // bytes per field of a slot (two rows)
+    static constexpr int SLOT = 4 * FSTRIDE;              // bytes per ring slot (eta, u, v, z of two rows)
+    static constexpr int WARP_SMEM = NPAIR * SLOT;
     // CTAs per SM the register budget must allow (FP32: 15 leaves the compiler
     // 136 registers; it uses at most 128, so 16 CTAs still fit)
     static constexpr int MINB = (sizeof(T) == 4 && CPT <= 2) ? 15 : 8;
@@ -286,20 +287,34 @@ __device__ __forceinline__ Cell<Vec<T, CPT>> cells(const Row<T, CPT>& r) {
     return c;
 }
 
-// Predicated issue of one ring row: lane 0 arms the barrier and starts the
-// four tile loads, if `want` (no branch).
+// The ring.  Ring row g (counted over the warp's items, even at an item's
+// start) sits in slot (g / 2) % NPAIR, at row g % 2 of each field's two; a
+// slot's two rows are one TMA box per field and complete one barrier.
+
+// Row base of ring row g (field f at + f * FSTRIDE); ODD = g % 2.
+template <class T, int CPT, int ODD>
+__device__ __forceinline__ const unsigned char* ring_row(const ItemCtx<T, CPT>& I, unsigned g) {
+    return I.ring + ((g >> 1) & (NPAIR - 1)) * Geo<T, CPT>::SLOT + ODD * Geo<T, CPT>::RSTRIDE;
+}
 template <class T, int CPT>
-__device__ __forceinline__ void issue_row(const ItemCtx<T, CPT>& I, int k, const CUtensorMap* tme,
-                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
-                                          bool want = true) {
+__device__ __forceinline__ const unsigned char* ring_row(const ItemCtx<T, CPT>& I, unsigned g) {
+    return I.ring + ((g >> 1) & (NPAIR - 1)) * Geo<T, CPT>::SLOT + (g & 1u) * Geo<T, CPT>::RSTRIDE;
+}
+
+// Predicated issue of the item's ring rows 2q and 2q + 1: lane 0 arms the
+// slot's barrier and starts the four two-row tile loads, if `want` (no branch).
+template <class T, int CPT>
+__device__ __forceinline__ void issue_pair(const ItemCtx<T, CPT>& I, int q, const CUtensorMap* tme,
+                                           const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
+                                           bool want = true) {
     using Gm = Geo<T, CPT>;
-    const unsigned g = I.g0 + (unsigned)k;
-    const unsigned bar = saddr(I.bars + (g & (NSLOT - 1)));
-    const unsigned dst = saddr(I.ring + (g & (NSLOT - 1)) * Gm::SLOT);
+    const unsigned sl = ((I.g0 >> 1) + (unsigned)q) & (NPAIR - 1);
+    const unsigned bar = saddr(I.bars + sl);
+    const unsigned dst = saddr(I.ring + sl * Gm::SLOT);
     const unsigned pred = (I.lane == 0 && want) ? 1u : 0u;
-    const int y = I.yoff + I.y0 - 2 + k;
+    const int y = I.yoff + I.y0 - 2 + 2 * q;
     asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}"
-                 ::"r"(pred), "r"(bar), "r"(4u * Gm::BW * (unsigned)sizeof(T)) : "memory");
+                 ::"r"(pred), "r"(bar), "r"(4u * 2u * (unsigned)Gm::RSTRIDE) : "memory");
     const CUtensorMap* maps[4] = {tme, tmu, tmv, tmz};
 #pragma unroll
     for (int f = 0; f < 4; ++f)
@@ -309,12 +324,20 @@ __device__ __forceinline__ void issue_row(const ItemCtx<T, CPT>& I, int k, const
             ::"r"(pred), "r"(dst + f * Gm::FSTRIDE), "l"(maps[f]), "r"(I.xb), "r"(y), "r"(bar) : "memory");
 }
 
-// Waits for ring row k; false (for the whole warp) when the wait gave up.
+// Barrier and phase parity of the item's ring rows 2q and 2q + 1.
 template <class T, int CPT>
-__device__ __forceinline__ bool wait_row(const ItemCtx<T, CPT>& I, int k) {
-    const unsigned g = I.g0 + (unsigned)k;
-    uint64_t* bar = I.bars + (g & (NSLOT - 1));
-    const unsigned par = (g / NSLOT) & 1u;
+__device__ __forceinline__ uint64_t* pair_bar(const ItemCtx<T, CPT>& I, int q, unsigned& par) {
+    const unsigned p = (I.g0 >> 1) + (unsigned)q;
+    par = (p / NPAIR) & 1u;
+    return I.bars + (p & (NPAIR - 1));
+}
+
+// Waits for the item's ring rows 2q and 2q + 1; false (for the whole warp)
+// when the wait gave up.
+template <class T, int CPT>
+__device__ __forceinline__ bool wait_pair(const ItemCtx<T, CPT>& I, int q) {
+    unsigned par;
+    uint64_t* bar = pair_bar(I, q, par);
     if (__all_sync(FULL, mbar_try(bar, par))) return true;
     const unsigned long long t0 = clock64();
     while (!__all_sync(FULL, mbar_try(bar, par)))
@@ -325,7 +348,7 @@ __device__ __forceinline__ bool wait_row(const ItemCtx<T, CPT>& I, int k) {
 template <class T, int CPT>
 __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CPT>& I, int row, int ny) {
     const int src = row < 0 ? 0 : (row >= ny ? ny - 1 : row);
-    return I.ring + ((I.g0 + (unsigned)(src - (I.y0 - 2))) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+    return ring_row(I, I.g0 + (unsigned)(src - (I.y0 - 2)));
 }
 
 // One ring row r (ring index k) of an item: y switch of row r-1, the
@@ -366,12 +389,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     const int lane = I.lane;
     const int r = I.y0 - 2 + k;
 
-    if (GEN) {  // the lean rows come in pairs, loaded and waited for by the caller
-        fence_async_smem();  // ring row k-4 (read two rows ago) is refilled next
-        issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz, k + NPRE < I.nr);
-        if (!wait_row<T, CPT>(I, k)) { timed_out = true; return; }
-    }
-    if (GEN && k < 2) return;
+    if (GEN && k < 2) return;  // the item's first pair of ring rows only loads
 
     // -------- level-n rows r, r-1, r-2 (ghost cells outside [0, ny)).  The
     // lean instantiation (GEN false) serves interior rows of items away from
@@ -379,10 +397,10 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     const bool brow = GEN && ((r - 2 <= 0) || (r >= ny));
     const bool edge = GEN && I.edge;
     const bool nfield = GEN ? A.n2 != nullptr : NF != 0;
-    const unsigned g = I.g0 + (unsigned)k;
-    const unsigned char* s0 = I.ring + ((g) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
-    const unsigned char* s1 = I.ring + ((g - 1u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
-    const unsigned char* s2 = I.ring + ((g - 2u) & (NSLOT - 1)) * Geo<T, CPT>::SLOT;
+    const unsigned g = I.g0 + (unsigned)k;  // g % 2 = PAR
+    const unsigned char* s0 = ring_row<T, CPT, PAR>(I, g);
+    const unsigned char* s1 = ring_row<T, CPT, 1 - PAR>(I, g - 1u);
+    const unsigned char* s2 = ring_row<T, CPT, PAR>(I, g - 2u);
     if (brow) {
         s0 = slot_clamped(I, r, ny);
         s1 = slot_clamped(I, r - 1, ny);
@@ -735,9 +753,10 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
                                         bool& timed_out, bool wet) {
     wet = TRY_WET && wet;
     fence_async_smem();  // the previous pass's rows were read through the generic proxy
-#pragma unroll
-    for (int k = 0; k < NPRE; ++k)
-        if (k < I.nr) issue_row<T, CPT>(I, k, tme, tmu, tmv, tmz);
+    const int nr = I.nr;
+    const int np = (nr + 1) / 2;  // pairs of ring rows (an odd count loads one row more)
+    issue_pair<T, CPT>(I, 0, tme, tmu, tmv, tmz);
+    issue_pair<T, CPT>(I, 1, tme, tmu, tmv, tmz, np > 1);
     Cy.NY[0] = Cy.NY[1] = Vec<T, CPT>(T(0));
 #pragma unroll
     for (int f = 0; f < 3; ++f) Cy.DX[0][f] = Cy.DX[1][f] = Vec<T, CPT>(T(0));
@@ -746,8 +765,7 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
 #pragma unroll
     for (int q = 0; q < 4; ++q) ia.side[q * 32] = T(0);
     bool ok = true, held = true;
-    const int nr = I.nr;
-    int drain_from = 0, issued = 0;  // after a failed wait or check: the rows to drain, [drain_from, issued)
+    int drain_from = 0, issued = 0;  // after a failed wait or check: the pairs to drain, [drain_from, issued)
     int k = 0;
     const int ny = A.G.ny;
     // Lean rows: pairs from the item's second on (the first, k = 0 and 1, only
@@ -760,15 +778,12 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
     const int khi = (I.edge || (TRY_WET && !wet)) ? 0 : min(nr - 1, ny - I.y0 + 1);
 #pragma unroll 1
     for (; k < nr; k += 2) {
+        const int q = k >> 1;
+        // the slot refilled held the pair before last, read up to the previous pair
+        fence_async_smem();
+        issue_pair<T, CPT>(I, q + 2, tme, tmu, tmv, tmz, q + 2 < np);
+        if (!wait_pair<T, CPT>(I, q)) { timed_out = true; drain_from = q; issued = min(np, q + 3); break; }
         if (k >= klo && k < khi) {
-            // both rows' loads and waits first, so that the two rows schedule as
-            // one block; the slots refilled were last read in the previous pair
-            fence_async_smem();
-            issue_row<T, CPT>(I, k + NPRE, tme, tmu, tmv, tmz, k + NPRE < nr);
-            issue_row<T, CPT>(I, k + 1 + NPRE, tme, tmu, tmv, tmz, k + 1 + NPRE < nr);
-            if (!wait_row<T, CPT>(I, k) || !wait_row<T, CPT>(I, k + 1)) {
-                timed_out = true; drain_from = k; issued = min(nr, k + 2 + NPRE); break;
-            }
 #define SWE_PAIR(NF, W)                                                                                           \
     row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);     \
     row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
@@ -776,32 +791,30 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
 #undef SWE_PAIR
         } else {
             row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);
-            if (timed_out) { drain_from = k; issued = min(nr, k + 1 + NPRE); break; }
-            if (k + 1 < nr) {  // the last row of an odd count runs alone
+            if (k + 1 < nr)  // the last row of an odd count runs alone
                 row_step<T, CPT, SX, SY, KAPPA, 1, true, 0, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out,
                                                                    ok, wet);
-                if (timed_out) { drain_from = k + 1; issued = min(nr, k + 2 + NPRE); break; }
-            }
         }
         if (TRY_WET && wet && !__all_sync(FULL, ok)) {
-            held = false; drain_from = min(nr, k + 2); issued = min(nr, k + 2 + NPRE); break;
+            held = false; drain_from = q + 1; issued = min(np, q + 3); break;
         }
     }
     const bool all_ok = held && __all_sync(FULL, ok);
-    if (TRY_WET && wet && held && !timed_out && !all_ok) { held = false; drain_from = nr; issued = nr; }
+    if (TRY_WET && wet && held && !timed_out && !all_ok) { held = false; drain_from = np; issued = np; }
     if (timed_out || !held) {
         // drain this pass's loads still in flight (bounded) before the ring is reused or left
         for (int q = drain_from; q < issued; ++q) {
-            const unsigned g = I.g0 + (unsigned)q;
+            unsigned par;
+            uint64_t* bar = pair_bar(I, q, par);
             unsigned long long t0 = clock64();
-            while (!mbar_try(I.bars + (g & (NSLOT - 1)), (g / NSLOT) & 1u))
+            while (!mbar_try(bar, par))
                 if (clock64() - t0 > WAIT_LIMIT / 8) break;
         }
-        I.g0 += (unsigned)issued;
+        I.g0 += 2u * (unsigned)issued;
         __syncwarp();
         return held ? 1 : 2;
     }
-    I.g0 += (unsigned)nr;
+    I.g0 += 2u * (unsigned)np;
     return all_ok ? 0 : 1;
 }
 
@@ -924,7 +937,7 @@ __global__ void __launch_bounds__(NWARP * 32, Geo<T, CPT>::MINB)
 k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtensorMap tmu,
         const __grid_constant__ CUtensorMap tmv, const __grid_constant__ CUtensorMap tmz, const Args<T> A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[NWARP][NSLOT];
+    __shared__ uint64_t bars[NWARP][NPAIR];
     __shared__ double sh_dt;
     __shared__ StepK<T> sh_S;  // the step's constants, divided once per CTA in FP64
     __shared__ bool sh_wet;    // this step runs the all-wet pass where an item's neighbourhood allows it
@@ -961,7 +974,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         }
     }
     if (lane == 0)
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[warp][s], 1);
+        for (int s = 0; s < NPAIR; ++s) mbar_init(&bars[warp][s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const double dt = sh_dt;
