@@ -382,7 +382,7 @@ void adj_step_raw(const swe_ctx* c, const GridK<T>& G, double dt, DevCtl* ctl, c
                   Planes4<T> Pc, Planes4<T> PX, Planes4<T> PY, T* ggn2, T* ggz, unsigned* dry) {
     const swe_params& p = c->p;
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
-    const StepK<T> S = make_stepk<T>(dt, p.dx, p.dy, p.g);
+    const StepK<T> S = make_stepk<T>(dt, 1.0 / p.dx, 1.0 / p.dy, p.g);
     // 1. the predicted state of this level
     k_plain_pred<T, SX, SY><<<grd, blk, 0, c->stream>>>(G, dtp, p.dx, p.dy, p.g, qn.e, qn.u, qn.v, (const T*)c->z,
                                                         (const T*)c->n2, qs.e, qs.u, qs.v, ctl, p.dx * p.dy);
@@ -576,7 +576,7 @@ swe_status adjoint_t(swe_ctx* c, int T_, const int64_t* gauges, int ng, const do
     if (!std::isfinite(L)) return afail(c, SWE_ERR_NONFINITE, "non-finite loss");
     *loss = L;
     std::vector<StepSlot> slots(T_ > 0 ? T_ : 1);
-    for (int s = 0; s < T_; ++s) slots[s] = make_slot(dts[s], p.dx, p.dy, p.g);
+    for (int s = 0; s < T_; ++s) slots[s] = make_slot(dts[s], 1.0 / p.dx, 1.0 / p.dy, p.g);
     if (T_ > 0)
         ACK(cudaMemcpyAsync(ssd, slots.data(), (size_t)T_ * sizeof(StepSlot), cudaMemcpyHostToDevice, c->stream));
     if (T_ > 0 && ng > 0)

@@ -61,6 +61,7 @@ struct BatchArgs {
     T* planes[2][3];       // eta, u, v of the two ping-pong copies
     const T* zp;           // bed
     double dx, dy, g, cfl, dt_max, area;
+    double rdx, rdy;  // 1/dx, 1/dy (divided on the host)
     long long step0;
     int nsteps, nitems, nscen, L, cur0, dir_cycle, dry_skip;
     int inflow_side[4];
@@ -130,7 +131,7 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
         const __grid_constant__ CUtensorMap zz, const BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[fz::NPAIR];
-    __shared__ double sh_tot[6];      // fz::Acc of the current item
+    __shared__ T sh_tot[6][32];       // fz::Acc of the current item
     __shared__ T sh_side[4][32];      // fz::ItemAcc::side
     const int lane = threadIdx.x & 31;
     if (lane == 0)
@@ -211,7 +212,7 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
             StepK<T> S;
             if (lane == 0) {
                 dt = scen_dt(B, bi.s, k);
-                S = make_stepk<T>(dt, B.dx, B.dy, B.g);
+                S = make_stepk<T>(dt, B.rdx, B.rdy, B.g);
             }
             dt = __shfl_sync(0xffffffffu, dt, 0);
             S.dt = __shfl_sync(0xffffffffu, S.dt, 0);
@@ -230,20 +231,28 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
             I.yoff = sc.row0;
             I.out_lane = sx > 0 ? lane != 0 : lane != 31;
             I.edge = (I.xw - 2 < 0) || (I.xw + Gm::W + 1 > sc.nx - 1);
-            Acc acc;
-            acc.p = sh_tot;
-            if (lane < 6) acc.p[lane] = 0.0;
-            __syncwarp();
+            Acc<T> acc;
+            acc.p = &sh_tot[0][lane];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) acc.p[m * 32] = T(0);
             acc.bad = false;
             bool all_wet;
             if (sx > 0) fz::run_item<T, CPT, 1, 1, KAPPA, false>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out, false, all_wet, &sh_side[0][lane]);
             else fz::run_item<T, CPT, -1, -1, KAPPA, false>(io, S, acc, I, Cy, me, mu, mv, &zz, timed_out, false, all_wet, &sh_side[0][lane]);
             // per-scenario reductions of this item
-            // the item's totals, reduced over the warp by run_item
-            __syncwarp();
+            // the item's totals, reduced over the warp in FP32, in FP64 from there
+            T w[6];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) w[m] = acc.p[m * 32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                w[0] = fmaxf(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
+#pragma unroll
+                for (int m = 1; m < 6; ++m) w[m] += __shfl_xor_sync(0xffffffffu, w[m], o);
+            }
             double v[6];
 #pragma unroll
-            for (int m = 0; m < 6; ++m) v[m] = acc.p[m];
+            for (int m = 0; m < 6; ++m) v[m] = (double)w[m];
             const bool bad = __any_sync(0xffffffffu, acc.bad);
             if (lane == 0) {
                 DevCtl* c = &B.ctl[bi.s];
@@ -457,6 +466,7 @@ BatchArgs make_args(const swe_batch* b, int nsteps) {
         for (int f = 0; f < 3; ++f) B.planes[q][f] = b->pl[q][f];
     B.zp = b->z;
     B.dx = p.dx; B.dy = p.dy; B.g = p.g; B.cfl = p.cfl; B.dt_max = p.dt_max; B.area = p.dx * p.dy;
+    B.rdx = 1.0 / p.dx; B.rdy = 1.0 / p.dy;
     B.step0 = b->step;
     B.nsteps = nsteps; B.nitems = b->nitems; B.nscen = b->count; B.L = b->L; B.cur0 = b->cur;
     B.dir_cycle = p.dir_cycle; B.dry_skip = p.dry_skip;

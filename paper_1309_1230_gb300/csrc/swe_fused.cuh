@@ -83,6 +83,7 @@ struct Args : ItemIO<T> {
     const double* dt_fixed;        // null: CFL step
     double* dt_hist;
     double dx, dy, g, cfl, dt_max, area;
+    double rdx, rdy;               // 1/dx, 1/dy (divided on the host)
     int s;                         // step within the call
     int slot_cur, slot_next, slot_zero;
     int nxs, nys, L, nitems;
@@ -205,11 +206,16 @@ struct Carry {
     Vec<T, CPT> DX[2][3];
 };
 
-// Totals that change once per item (the warp's FP64 totals) or only in
-// boundary rows (an item's side tallies, one slot per lane at stride 32) sit
-// in shared memory, so that they hold no registers through the row loop.
-struct Acc {  // per-warp totals over its items, FP64: p[m], m = 0 smax, 1 clamp, 2..5 sides W, E, S, N
-    double* p;
+// Totals that change once per item (a lane's totals over the warp's items)
+// or only in boundary rows (an item's side tallies) sit in shared memory,
+// one slot per lane at stride 32, so that they hold no registers through the
+// row loop.  They are kept in the state's real type and reduced over the
+// warp in FP64 once, at the end of the launch: GB300's FP64 pipe takes tens
+// of cycles per warp instruction, and a reduction per item kept it busy a
+// fifth of the time.
+template <class T>
+struct Acc {  // p[m * 32], m = 0 smax, 1 clamp, 2..5 sides W, E, S, N
+    T* p;
     bool bad;
 };
 
@@ -822,10 +828,10 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
 // all_wet: whether every output cell is.  try_wet: run the item on the
 // all-wet assumption first, and again in the general form where it fails
 // (only when TRY_WET: the FP32 form, where the wet/dry selects are a large
-// share of the row's instructions).  The item's tallies are reduced over the
-// warp in FP64 and added to the warp's totals, acc.p[m] (lane 0 keeps them).
+// share of the row's instructions).  The item's tallies are added to the
+// lane's totals acc.p[m * 32].
 template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
-__device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc& acc, ItemCtx<T, CPT>& I,
+__device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, Acc<T>& acc, ItemCtx<T, CPT>& I,
                                          Carry<T, CPT>& Cy, const CUtensorMap* tme, const CUtensorMap* tmu,
                                          const CUtensorMap* tmv, const CUtensorMap* tmz, bool& timed_out,
                                          bool try_wet, bool& all_wet, T* side) {
@@ -844,21 +850,12 @@ __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, 
         w = false;
     }
     all_wet = st == 0;
-    double v[6] = {(double)ia.smax, (double)ia.clamp, (double)ia.side[0], (double)ia.side[32], (double)ia.side[64],
-                   (double)ia.side[96]};
+    acc.p[0] = tmax(acc.p[0], ia.smax);
+    acc.p[32] += ia.clamp;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(FULL, v[0], o));
-#pragma unroll
-        for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(FULL, v[m], o);
-    }
-    if (I.lane == 0) {
-        acc.p[0] = fmax(acc.p[0], v[0]);
-#pragma unroll
-        for (int m = 1; m < 6; ++m) acc.p[m] += v[m];
-    }
+    for (int q = 0; q < 4; ++q) acc.p[(2 + q) * 32] += ia.side[q * 32];
     acc.bad = acc.bad || ia.bad;
-    return v[0] > 0.0;
+    return __any_sync(FULL, ia.smax > T(0));
 }
 
 // The work-item loop of one launch.  TRY_WET: items whose neighbourhood was
@@ -868,7 +865,7 @@ __device__ __forceinline__ bool run_item(const ItemIO<T>& A, const StepK<T>& S, 
 template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
 __device__ __forceinline__ void item_loop(const Args<T>& A, const StepK<T>& S, const CUtensorMap* tme,
                                           const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
-                                          unsigned char* ring, uint64_t* bars, int lane, Acc& acc, bool& timed_out,
+                                          unsigned char* ring, uint64_t* bars, int lane, Acc<T>& acc, bool& timed_out,
                                           unsigned* wc, T* side) {
     ItemCtx<T, CPT> I;
     I.ring = ring;
@@ -943,7 +940,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     __shared__ bool sh_wet;    // this step runs the all-wet pass where an item's neighbourhood allows it
     __shared__ unsigned sh_wc[2];  // the CTA's interior items with and without an all-wet neighbourhood
     __shared__ double red[NWARP][6];
-    __shared__ double sh_tot[NWARP][6];   // Acc
+    __shared__ T sh_tot[NWARP][6][32];    // Acc
     __shared__ T sh_side[NWARP][4][32];   // ItemAcc::side
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -951,7 +948,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         double dt = A.dt_fixed ? A.dt_fixed[A.s]
                                : dt_from_speed(__longlong_as_double((long long)A.ctl->smax[A.slot_cur]), A.cfl, A.dt_max);
         sh_dt = dt;
-        sh_S = make_stepk<T>(dt, A.dx, A.dy, A.g);
+        sh_S = make_stepk<T>(dt, A.rdx, A.rdy, A.g);
         // The all-wet pass and the general lean rows are two large blocks of
         // code; where both run in one step they contend for the instruction
         // cache, which costs more than the pass saves.  So the pass runs only
@@ -981,9 +978,10 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     const StepK<T> S = sh_S;
     const bool use_wet = sh_wet;
 
-    Acc acc;
-    acc.p = sh_tot[warp];
-    if (lane < 6) acc.p[lane] = 0.0;
+    Acc<T> acc;
+    acc.p = &sh_tot[warp][0][lane];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) acc.p[m * 32] = T(0);
     __syncwarp();
     acc.bad = false;
     bool timed_out = false;
@@ -1003,7 +1001,13 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     __syncwarp();
     double v[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) v[m] = acc.p[m];
+    for (int m = 0; m < 6; ++m) v[m] = (double)acc.p[m * 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmax(v[0], __shfl_xor_sync(FULL, v[0], o));
+#pragma unroll
+        for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(FULL, v[m], o);
+    }
     const bool bad = __any_sync(FULL, acc.bad);
     const bool tmo = __any_sync(FULL, timed_out);
     if (lane == 0) {
@@ -1067,6 +1071,7 @@ cudaError_t launch_t(swe_ctx* c, const Plan& pl, int s, long long k) {
     A.dt_fixed = c->dt_fixed_cap > 0 ? c->dt_fixed : nullptr;
     A.dt_hist = c->dt_hist;
     A.dx = p.dx; A.dy = p.dy; A.g = p.g; A.cfl = p.cfl; A.dt_max = p.dt_max; A.area = p.dx * p.dy;
+    A.rdx = 1.0 / p.dx; A.rdy = 1.0 / p.dy;
     A.s = s;
     A.slot_cur = (int)(k % 3); A.slot_next = (int)((k + 1) % 3); A.slot_zero = (int)((k + 2) % 3);
     A.nxs = pl.nxs; A.nys = pl.nys; A.L = pl.L; A.nitems = pl.nitems; A.nfull = p.ny / pl.L;

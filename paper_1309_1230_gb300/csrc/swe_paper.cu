@@ -89,9 +89,9 @@ __device__ __forceinline__ Cell<T> nbr(const GridK<T>& G, const T* e, const T* u
 
 // Step size and clock bookkeeping of step s (S2's result on the device).
 __global__ void k_paper_dt(DevCtl* ctl, const double* dtv, int from_smax, int slot, int slot_next, int s,
-                           double* dt_hist, double cfl, double dt_max, double dx, double dy, double g) {
+                           double* dt_hist, double cfl, double dt_max, double rdx, double rdy, double g) {
     const double dt = from_smax ? dt_from_speed(__longlong_as_double((long long)ctl->smax[slot]), cfl, dt_max) : *dtv;
-    ctl->cur = make_slot(dt, dx, dy, g);
+    ctl->cur = make_slot(dt, rdx, rdy, g);
     ctl->dt_last = dt;
     ctl->t += dt;
     ctl->dt_min = fmin(ctl->dt_min, dt);
@@ -541,7 +541,7 @@ cudaError_t step_t(swe_ctx* c, Scratch<T>* q, int s, long long k) {
             return err;
     }
     k_paper_dt<<<1, 1, 0, c->stream>>>(c->ctl, dtv, (!fixed && devdt) ? 1 : 0, slot, slot_next, s, c->dt_hist, p.cfl,
-                                       p.dt_max, p.dx, p.dy, p.g);
+                                       p.dt_max, 1.0 / p.dx, 1.0 / p.dy, p.g);
     const double* dtp = &c->ctl->cur.dt;
     const dim3 blk(BX), grd((p.nx + BX - 1) / BX, p.ny);
     const int nside = p.nx > p.ny ? p.nx : p.ny;

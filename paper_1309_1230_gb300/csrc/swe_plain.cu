@@ -270,7 +270,7 @@ cudaError_t swe_plain_step_f32_raw(const swe_params* p, int pitch, const float* 
     for (int s = 0; s < 4; ++s) { G.bc[s] = p->bc[s]; G.qin[s] = (float)p->q_in[s]; }
     const size_t n = (size_t)p->nx * p->ny;
     if (!dt_fixed) k_prologue<float><<<util_blocks(n), 256, 0, st>>>(G, e, u, v, z, ctl, 0);
-    k_plain_dt<<<1, 1, 0, st>>>(ctl, 0, 1, dt_fixed, 0, dt_hist, p->cfl, p->dt_max, p->dx, p->dy, p->g);
+    k_plain_dt<<<1, 1, 0, st>>>(ctl, 0, 1, dt_fixed, 0, dt_hist, p->cfl, p->dt_max, 1.0 / p->dx, 1.0 / p->dy, p->g);
     int sx, sy;
     step_dirs(p->dir_cycle, 0, &sx, &sy);
     dim3 blk(32, 8), grd((p->nx + 31) / 32, (p->ny + 7) / 8);

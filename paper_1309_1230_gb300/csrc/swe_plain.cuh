@@ -30,11 +30,11 @@ __device__ __forceinline__ T warp_max(T x) {
 
 // Step size of step s of a call: replayed or from the level's CFL reduction.
 static __global__ void k_plain_dt(DevCtl* ctl, int slot, int slot_next, const double* dt_fixed, int s,
-                           double* dt_hist, double cfl, double dt_max, double dx, double dy, double g) {
+                           double* dt_hist, double cfl, double dt_max, double rdx, double rdy, double g) {
     double dt;
     if (dt_fixed) dt = dt_fixed[s];
     else dt = dt_from_speed(__longlong_as_double((long long)ctl->smax[slot]), cfl, dt_max);
-    ctl->cur = make_slot(dt, dx, dy, g);
+    ctl->cur = make_slot(dt, rdx, rdy, g);
     ctl->dt_last = dt;
     ctl->t += dt;
     ctl->dt_min = fmin(ctl->dt_min, dt);
@@ -292,7 +292,7 @@ static cudaError_t plain_step_t(swe_ctx* c, int s, long long k) {
     GridK<T> G = grid_of<T>(c);
     int slot = (int)(k % 3), slot_next = (int)((k + 1) % 3);
     k_plain_dt<<<1, 1, 0, c->stream>>>(c->ctl, slot, slot_next, c->dt_fixed_cap > 0 && c->dt_fixed ? c->dt_fixed : nullptr,
-                                       s, c->dt_hist, p.cfl, p.dt_max, p.dx, p.dy, p.g);
+                                       s, c->dt_hist, p.cfl, p.dt_max, 1.0 / p.dx, 1.0 / p.dy, p.g);
     dim3 blk(32, 8), grd((p.nx + 31) / 32, (p.ny + 7) / 8);
     const int a = c->cur, b = 1 - c->cur;
     const double area = p.dx * p.dy;
