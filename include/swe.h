@@ -66,7 +66,8 @@ typedef enum {
     SWE_ERR_NEGDEPTH = 4,   /* input depth below -1e-12 m */
     SWE_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
     SWE_ERR_STATE = 6,      /* call out of order, or context poisoned */
-    SWE_ERR_UNSUPPORTED = 7 /* configuration the called entry point does not handle */
+    SWE_ERR_UNSUPPORTED = 7, /* configuration the called entry point does not handle */
+    SWE_ERR_CHECK = 8       /* a device-side index or alignment check failed (checked builds only) */
 } swe_status;
 
 typedef enum { SWE_BC_WALL = 0, SWE_BC_INFLOW = 1, SWE_BC_OUTFLOW = 2 } swe_bc;
@@ -96,6 +97,9 @@ typedef enum {
 #define SWE_FLAG_NONFINITE 1u
 #define SWE_FLAG_TIMEOUT 2u
 #define SWE_FLAG_CLAMPED 4u
+#define SWE_FLAG_CHECK 8u      /* checked builds: a shared-memory read, global store or TMA
+                                  coordinate of the fused or batched row step was out of range
+                                  or misaligned; the access was skipped */
 
 typedef struct {
     int32_t nx, ny;         /* cells in x and y, >= 1 */

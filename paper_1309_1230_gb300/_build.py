@@ -18,6 +18,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswe.so")
+# The checked build (-DSWE_CHECKED): device-side index and alignment checks in
+# the fused and batched row steps that record a failure in the step flags and
+# skip the access, and NaN in every byte of the planes' padding; for tests.
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+LIB_CHECKED = os.path.join(CHECKED_DIR, "libswe_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 arithmetic uses approximate division/square root with flush-to-zero
@@ -45,20 +50,23 @@ def _deps():
         os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    out_dir = CHECKED_DIR if checked else OUT_DIR
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DSWE_CHECKED"] if checked else [])
 
     def comp(pair):
         src, obj = pair
@@ -74,13 +82,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(f"== {os.path.basename(s)}\n{r.stdout}{r.stderr}")
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(os.path.basename(s) for s, _ in failed))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

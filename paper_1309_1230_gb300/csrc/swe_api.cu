@@ -148,6 +148,7 @@ const char* swe_status_string(swe_status s) {
     case SWE_ERR_TIMEOUT: return "device wait timed out";
     case SWE_ERR_STATE: return "call out of order or context poisoned";
     case SWE_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SWE_ERR_CHECK: return "device-side check failed";
     }
     return "unknown status";
 }
@@ -190,15 +191,22 @@ swe_status swe_create(const swe_params* p, swe_ctx** out) {
         c->own_stream = true;
     }
     const size_t bytes = c->plane * c->real_size;
+#ifdef SWE_CHECKED
+    // every byte 0xff (a NaN in FP32 and FP64) until set: a read of a plane's
+    // padding or of a cell never written shows as a non-finite state
+    const int fill = 0xff;
+#else
+    const int fill = 0;
+#endif
     for (int b = 0; b < 2; ++b) {
         void** bufs[3] = {&c->eta[b], &c->u[b], &c->v[b]};
         for (void** q : bufs) {
             if ((e = cudaMalloc(q, bytes)) != cudaSuccess) return bail(e, "cudaMalloc state");
-            if ((e = cudaMemset(*q, 0, bytes)) != cudaSuccess) return bail(e, "cudaMemset");
+            if ((e = cudaMemset(*q, fill, bytes)) != cudaSuccess) return bail(e, "cudaMemset");
         }
     }
     if ((e = cudaMalloc(&c->z, bytes)) != cudaSuccess) return bail(e, "cudaMalloc bed");
-    if ((e = cudaMemset(c->z, 0, bytes)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMemset(c->z, fill, bytes)) != cudaSuccess) return bail(e, "cudaMemset");
     if ((e = cudaMalloc(&c->z64, (size_t)p->nx * p->ny * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc bed64");
     if ((e = cudaMemset(c->z64, 0, (size_t)p->nx * p->ny * sizeof(double))) != cudaSuccess) return bail(e, "cudaMemset");
     if (p->kernel == SWE_KERNEL_PLAIN) {
@@ -445,6 +453,8 @@ swe_status swe_step(swe_ctx* c, int32_t nsteps, const double* dt_fixed, double* 
     swe_step_info local;
     if ((s = fill_info(c, info ? info : &local, info != nullptr)) != SWE_OK) return s;
     if (c->h_ctl->flags & SWE_FLAG_TIMEOUT) return fail(c, SWE_ERR_TIMEOUT, "a device-side wait gave up");
+    if (c->h_ctl->flags & SWE_FLAG_CHECK)
+        return fail(c, SWE_ERR_CHECK, "a device-side index or alignment check failed (checked build)");
     if ((c->h_ctl->flags & SWE_FLAG_NONFINITE) || (info && (info->flags & SWE_FLAG_NONFINITE)))
         return fail(c, SWE_ERR_NONFINITE, "non-finite value in the state");
     return SWE_OK;

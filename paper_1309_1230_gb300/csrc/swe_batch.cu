@@ -139,11 +139,15 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncwarp();
 
+    __shared__ unsigned sh_chk;       // checked builds: a check of the row step failed (fz::SWE_CHK)
+    if (lane == 0) sh_chk = 0u;
+    __syncwarp();
     ItemCtx<T, CPT> I;
     I.ring = smem;
     I.bars = bars;
     I.lane = lane;
     I.g0 = 0;
+    I.chk = &sh_chk;
     Carry<T, CPT> Cy;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
@@ -263,6 +267,7 @@ k_batch(const __grid_constant__ CUtensorMap eA, const __grid_constant__ CUtensor
                 if (v[4] != 0.0) atomicAdd(&c->bflux[2], v[4] * dt * B.dx);
                 if (v[5] != 0.0) atomicAdd(&c->bflux[3], v[5] * dt * B.dx);
                 if (bad) atomicOr(&c->flags, (unsigned)SWE_FLAG_NONFINITE);
+                if (sh_chk) { atomicOr(&c->flags, (unsigned)SWE_FLAG_CHECK); sh_chk = 0u; }
                 fl_out[bi.fi] = (v[0] > 0.0 ? 1u : 0u) | (dry ? 2u : 0u);
             }
             if (timed_out) break;
@@ -618,13 +623,19 @@ swe_status swe_batch_create(const swe_params* p, int32_t count, const int32_t* n
         if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
         b->own_stream = true;
     }
+#ifdef SWE_CHECKED
+    // every byte 0xff (a NaN) until set: a read beyond a scenario's cells shows
+    const int fill = 0xff;
+#else
+    const int fill = 0;
+#endif
     for (int q = 0; q < 2; ++q)
         for (int f = 0; f < 3; ++f) {
             if ((e = cudaMalloc(&b->pl[q][f], b->plane * sizeof(T))) != cudaSuccess) return bail("planes", e);
-            if ((e = cudaMemset(b->pl[q][f], 0, b->plane * sizeof(T))) != cudaSuccess) return bail("memset", e);
+            if ((e = cudaMemset(b->pl[q][f], fill, b->plane * sizeof(T))) != cudaSuccess) return bail("memset", e);
         }
     if ((e = cudaMalloc(&b->z, b->plane * sizeof(T))) != cudaSuccess) return bail("bed", e);
-    if ((e = cudaMemset(b->z, 0, b->plane * sizeof(T))) != cudaSuccess) return bail("memset", e);
+    if ((e = cudaMemset(b->z, fill, b->plane * sizeof(T))) != cudaSuccess) return bail("memset", e);
     b->order.resize(count);
     for (int q = 0; q < count; ++q) b->order[q] = q;
     std::stable_sort(b->order.begin(), b->order.end(),
@@ -803,6 +814,7 @@ swe_status swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos) {
     }
     if (any & SWE_FLAG_TIMEOUT) return bfail(b, SWE_ERR_TIMEOUT, "grid barrier or load wait gave up");
     if (any & SWE_FLAG_NONFINITE) return bfail(b, SWE_ERR_NONFINITE, "non-finite value in a scenario");
+    if (any & SWE_FLAG_CHECK) return bfail(b, SWE_ERR_CHECK, "a device-side index or alignment check failed (checked build)");
     return SWE_OK;
 }
 

@@ -236,7 +236,18 @@ struct ItemCtx {
     bool st_lane;                // the lane outputs and its first cell is in the grid
     int plo, phi;                // rows of the item whose predicted clamps this item tallies
     unsigned g0;
+    unsigned* chk;               // checked builds: set when a check fails (shared memory)
 };
+
+// Checked builds (SWE_CHECKED): a failed index or alignment check of the row
+// step sets *I.chk and the access is made safe instead (a clamped column, the
+// ring's first row, a store left out, an aligned TMA coordinate); the kernel
+// reports SWE_FLAG_CHECK.  Nothing traps.  Other builds compile the checks out.
+#ifdef SWE_CHECKED
+#define SWE_CHK(I, cond) ((cond) ? true : (*(I).chk = 1u, false))
+#else
+#define SWE_CHK(I, cond) true
+#endif
 
 template <class T, int CPT>
 __device__ __forceinline__ void ld_row(const unsigned char* slot, int col, Row<T, CPT>& r) {
@@ -319,6 +330,8 @@ __device__ __forceinline__ void issue_pair(const ItemCtx<T, CPT>& I, int q, cons
     const unsigned dst = saddr(I.ring + sl * Gm::SLOT);
     const unsigned pred = (I.lane == 0 && want) ? 1u : 0u;
     const int y = I.yoff + I.y0 - 2 + 2 * q;
+    int xb = I.xb;
+    if (!SWE_CHK(I, (xb * (int)sizeof(T)) % 16 == 0)) xb &= ~(Gm::ALIGN - 1);  // TMA x: 16-byte multiple
     asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}"
                  ::"r"(pred), "r"(bar), "r"(4u * 2u * (unsigned)Gm::RSTRIDE) : "memory");
     const CUtensorMap* maps[4] = {tme, tmu, tmv, tmz};
@@ -327,7 +340,7 @@ __device__ __forceinline__ void issue_pair(const ItemCtx<T, CPT>& I, int q, cons
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %0, 0;\n"
             " @p cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%1], [%2, {%3, %4}], [%5];\n}"
-            ::"r"(pred), "r"(dst + f * Gm::FSTRIDE), "l"(maps[f]), "r"(I.xb), "r"(y), "r"(bar) : "memory");
+            ::"r"(pred), "r"(dst + f * Gm::FSTRIDE), "l"(maps[f]), "r"(xb), "r"(y), "r"(bar) : "memory");
 }
 
 // Barrier and phase parity of the item's ring rows 2q and 2q + 1.
@@ -412,10 +425,25 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         s1 = slot_clamped(I, r - 1, ny);
         s2 = slot_clamped(I, r - 2, ny);
     }
+    int col = I.col;
+#ifdef SWE_CHECKED
+    {   // the rows in the ring, their columns col - 2 .. col + CPT + 1 in the row, vector-aligned
+        using Gm = Geo<T, CPT>;
+        const unsigned char* sp[3] = {s0, s1, s2};
+        bool in = true;
+        for (int q = 0; q < 3; ++q) {  // a slot's first or second row
+            const long off = (long)(sp[q] - I.ring), r = off % Gm::SLOT;
+            in = in && off >= 0 && off + 3 * Gm::FSTRIDE + Gm::RSTRIDE <= Gm::WARP_SMEM &&
+                 (r == 0 || r == Gm::RSTRIDE);
+        }
+        if (!SWE_CHK(I, in)) s0 = s1 = s2 = I.ring;
+        if (!SWE_CHK(I, col >= 2 && col + CPT + 2 <= Gm::BW && col % CPT == 0)) col = 2 * CPT;
+    }
+#endif
     Row<T, CPT> R0, R1, R2;
-    ld_row<T, CPT>(s0, I.col, R0);
-    ld_row<T, CPT>(s1, I.col, R1);
-    ld_row<T, CPT>(s2, I.col, R2);
+    ld_row<T, CPT>(s0, col, R0);
+    ld_row<T, CPT>(s1, col, R1);
+    ld_row<T, CPT>(s2, col, R2);
     if (brow) {
         if (r < 0) ghost_row(R0, SIDE_S, G); else if (r >= ny) ghost_row(R0, SIDE_N, G);
         if (r - 1 < 0) ghost_row(R1, SIDE_S, G); else if (r - 1 >= ny) ghost_row(R1, SIDE_N, G);
@@ -447,7 +475,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         const Row<T, CPT>& yn = SY > 0 ? R0 : R2;
         const V hyn = SY > 0 ? h0 : h2;
         // x neighbours on the predictor's side: the lane's next cells, the outer one from the ring
-        const int hcol = SX > 0 ? I.col + CPT : I.col - 1;
+        const int hcol = SX > 0 ? col + CPT : col - 1;
         Row<T, CPT> xn;
         xn.e = shift<SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, hcol), true);
         xn.u = shift<SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, hcol), true);
@@ -523,7 +551,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             // x dissipation of row r-1; the outer neighbour on the other side
             // from the ring as well
             Row<T, CPT> xo;
-            const int ocol = SX > 0 ? I.col - 1 : I.col + CPT;
+            const int ocol = SX > 0 ? col - 1 : col + CPT;
             xo.e = shift<-SX, T, CPT>(c.e, ld1<T, CPT>(s1, 0, ocol), true);
             xo.u = shift<-SX, T, CPT>(c.u, ld1<T, CPT>(s1, 1, ocol), true);
             xo.v = shift<-SX, T, CPT>(c.v, ld1<T, CPT>(s1, 2, ocol), true);
@@ -546,12 +574,12 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             // adjacent lane's (the edge lane there never outputs)
             T nu_lo, nu_hi;
             if (SX > 0) {
-                T h2x = ld1<T, CPT>(s1, 0, I.col + CPT + 1) - ld1<T, CPT>(s1, 3, I.col + CPT + 1);
+                T h2x = ld1<T, CPT>(s1, 0, col + CPT + 1) - ld1<T, CPT>(s1, 3, col + CPT + 1);
                 if (edge && I.x0c + CPT == nx - 1) h2x = hr[CPT - 1];
                 nu_hi = nu_switch(h1[CPT - 1], hr[CPT - 1], h2x);
                 nu_lo = shup(nuc[CPT - 1]);
             } else {
-                T h2x = ld1<T, CPT>(s1, 0, I.col - 2) - ld1<T, CPT>(s1, 3, I.col - 2);
+                T h2x = ld1<T, CPT>(s1, 0, col - 2) - ld1<T, CPT>(s1, 3, col - 2);
                 if (edge && I.x0c - 1 == 0) h2x = hl[0];
                 nu_lo = nu_switch(h2x, hl[0], h1[0]);
                 nu_hi = shdn(nuc[0]);
@@ -569,13 +597,25 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
                 for (int j = 0; j < CPT; ++j)
                     if (I.x0c + j + 1 >= nx) eps[j] = T(0);
             }
-            const V fr[3] = {dflux(eps, Rr.e, c.e), dflux(eps, Rr.u, c.u), dflux(eps, Rr.v, c.v)};
+            V fr[3] = {dflux(eps, Rr.e, c.e), dflux(eps, Rr.u, c.u), dflux(eps, Rr.v, c.v)};
             // west face of the first cell; the others' west faces are their left neighbours' east faces
             T e0;
             if (WA) e0 = face_eps_wet(nu_lo, nuc[0]);
             else e0 = face_eps(hl[0] > hd, h1[0] > hd, nu_lo, nuc[0]);
             if (edge && I.x0c - 1 < 0) e0 = T(0);
-            const T fl0[3] = {dflux(e0, c.e[0], L.e[0]), dflux(e0, c.u[0], L.u[0]), dflux(e0, c.v[0], L.v[0])};
+            T fl0[3] = {dflux(e0, c.e[0], L.e[0]), dflux(e0, c.u[0], L.u[0]), dflux(e0, c.v[0], L.v[0])};
+            if (edge) {
+                // a face on the x boundary carries +0, whatever lies beyond the grid
+                // (the one-thread-per-cell kernel's difference of a cell with its
+                // clamped self)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j)
+                        if (I.x0c + j + 1 >= nx) fr[f][j] = T(0);
+                    if (I.x0c - 1 < 0) fl0[f] = T(0);
+                }
+            }
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 V west;
@@ -639,7 +679,8 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         V gn2v;
         if (nfield) {
             const int xc = I.x0c < 0 ? 0 : (I.x0c > G.pitch - CPT ? G.pitch - CPT : I.x0c);
-            ld_vec<T, CPT>(A.n2 + (size_t)C * G.pitch + xc, gn2v);
+            const int cr = SWE_CHK(I, C >= 0 && C < ny) ? C : 0;
+            ld_vec<T, CPT>(A.n2 + (size_t)cr * G.pitch + xc, gn2v);
         } else {
             gn2v = V(G.gn2);
         }
@@ -660,7 +701,10 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         }
         // a lean row of an item's first pair (k < 4) runs the corrector on rows
         // of the item above: nothing of it is stored or tallied
-        const bool st = I.st_lane && (GEN || k >= 4);
+        bool st = I.st_lane && (GEN || k >= 4);
+#ifdef SWE_CHECKED
+        if (st && !SWE_CHK(I, C >= 0 && C < ny && I.x0c >= 0 && I.x0c + CPT <= G.pitch && I.x0c % CPT == 0)) st = false;
+#endif
         // the new cells the item outputs are wet (the fix below keeps a cell
         // whose depth is above h_dry as it is)
         const V hn = oe - cs.z;
@@ -673,11 +717,11 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         else ad = wetdry_fix(oe, ou, ov, cs.z, hd);
         V spj = cfl_speed<WA>(oe, ou, ov, cs.z, G);
         const V sum = oe + ou + ov;
-        const V dsum = sum - sum;  // NaN for a non-finite cell
-        if (edge) {
+        V dsum = sum - sum;  // NaN for a non-finite cell
+        if (edge) {  // a lane's cells beyond the grid are computed, not output
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
-                if (I.x0c + j >= nx) { ad[j] = T(0); spj[j] = T(0); }
+                if (I.x0c + j >= nx) { ad[j] = T(0); spj[j] = T(0); dsum[j] = T(0); }
         }
         // the row's speed maximum (speeds are >= 0 and never NaN in a finite
         // state; a NaN speed is left out, as the max of fmax does) and the sum of
@@ -866,10 +910,11 @@ template <class T, int CPT, int SX, int SY, bool KAPPA, bool TRY_WET>
 __device__ __forceinline__ void item_loop(const Args<T>& A, const StepK<T>& S, const CUtensorMap* tme,
                                           const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
                                           unsigned char* ring, uint64_t* bars, int lane, Acc<T>& acc, bool& timed_out,
-                                          unsigned* wc, T* side) {
+                                          unsigned* wc, T* side, unsigned* chk) {
     ItemCtx<T, CPT> I;
     I.ring = ring;
     I.bars = bars;
+    I.chk = chk;
     I.lane = lane;
     I.out_lane = SX > 0 ? lane != 0 : lane != 31;
     I.g0 = 0;
@@ -939,6 +984,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     __shared__ StepK<T> sh_S;  // the step's constants, divided once per CTA in FP64
     __shared__ bool sh_wet;    // this step runs the all-wet pass where an item's neighbourhood allows it
     __shared__ unsigned sh_wc[2];  // the CTA's interior items with and without an all-wet neighbourhood
+    __shared__ unsigned sh_chk;    // checked builds: a check of the row step failed
     __shared__ double red[NWARP][6];
     __shared__ T sh_tot[NWARP][6][32];    // Acc
     __shared__ T sh_side[NWARP][4][32];   // ItemAcc::side
@@ -958,6 +1004,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         const unsigned* wc = A.ctl->wcnt[A.slot_cur];
         sh_wet = (unsigned long long)wc[1] * WET_SHARE <= (unsigned long long)wc[0];
         sh_wc[0] = sh_wc[1] = 0u;
+        sh_chk = 0u;
         if (blockIdx.x == 0) {
             DevCtl* c = A.ctl;
             c->dt_last = dt;
@@ -988,26 +1035,34 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
     if constexpr (sizeof(T) == 4) {
         if (use_wet)
             item_loop<T, CPT, SX, SY, KAPPA, true>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
-                                                   bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+                                                   bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane],
+                                                   &sh_chk);
         else
             item_loop<T, CPT, SX, SY, KAPPA, false>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
-                                                    bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+                                                    bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane],
+                                                   &sh_chk);
     } else {
         item_loop<T, CPT, SX, SY, KAPPA, false>(A, S, &tme, &tmu, &tmv, &tmz, smem + warp * Geo<T, CPT>::WARP_SMEM,
-                                                bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane]);
+                                                bars[warp], lane, acc, timed_out, sh_wc, &sh_side[warp][0][lane],
+                                                   &sh_chk);
     }
 
     // ---- reductions: warp, CTA, then one atomic per CTA
     __syncwarp();
-    double v[6];
+    // the lanes' totals reduced over the warp in the real type, in FP64 from
+    // there on (lane 0)
+    T w[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) v[m] = (double)acc.p[m * 32];
+    for (int m = 0; m < 6; ++m) w[m] = acc.p[m * 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(FULL, v[0], o));
+        w[0] = tmax(w[0], __shfl_xor_sync(FULL, w[0], o));
 #pragma unroll
-        for (int m = 1; m < 6; ++m) v[m] += __shfl_xor_sync(FULL, v[m], o);
+        for (int m = 1; m < 6; ++m) w[m] += __shfl_xor_sync(FULL, w[m], o);
     }
+    double v[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) v[m] = (double)w[m];
     const bool bad = __any_sync(FULL, acc.bad);
     const bool tmo = __any_sync(FULL, timed_out);
     if (lane == 0) {
@@ -1015,6 +1070,7 @@ k_fused(const __grid_constant__ CUtensorMap tme, const __grid_constant__ CUtenso
         for (int m = 0; m < 6; ++m) red[warp][m] = v[m];
         if (bad) atomicOr(&A.ctl->flags, (unsigned)SWE_FLAG_NONFINITE);
         if (tmo) atomicOr(&A.ctl->flags, (unsigned)SWE_FLAG_TIMEOUT);
+        if (sh_chk) atomicOr(&A.ctl->flags, (unsigned)SWE_FLAG_CHECK);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

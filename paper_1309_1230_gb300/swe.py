@@ -21,12 +21,12 @@ import numpy as np
 from . import _build
 
 SWE_OK, SWE_ERR_ARG, SWE_ERR_CUDA, SWE_ERR_NONFINITE = 0, 1, 2, 3
-SWE_ERR_NEGDEPTH, SWE_ERR_TIMEOUT, SWE_ERR_STATE, SWE_ERR_UNSUPPORTED = 4, 5, 6, 7
+SWE_ERR_NEGDEPTH, SWE_ERR_TIMEOUT, SWE_ERR_STATE, SWE_ERR_UNSUPPORTED, SWE_ERR_CHECK = 4, 5, 6, 7, 8
 SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_OUTFLOW = 0, 1, 2
 SWE_FP64, SWE_FP32 = 0, 1
 SWE_KERNEL_FUSED, SWE_KERNEL_PLAIN, SWE_KERNEL_PAPER, SWE_KERNEL_PAPER_DEVDT = 0, 1, 2, 3
 SWE_KERNEL_PAPER_SHARED, SWE_KERNEL_PAPER_SHARED_DEVDT = 4, 5
-SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED = 1, 2, 4
+SWE_FLAG_NONFINITE, SWE_FLAG_TIMEOUT, SWE_FLAG_CLAMPED, SWE_FLAG_CHECK = 1, 2, 4, 8
 SWE_NOALLOC_MAX_CELLS = 1 << 20
 
 
@@ -111,6 +111,15 @@ def library_path() -> str:
     return _build.LIB
 
 
+def _open(path: str) -> ctypes.CDLL:
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
     """Loads libswe.so (building it first if it is missing or stale)."""
     global _lib
@@ -121,13 +130,24 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                 _build.build()
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library {path} is missing; run the build first")
-            lib = ctypes.CDLL(path)
-            for name, (res, args) in _SIGS.items():
-                f = getattr(lib, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = lib
+            _lib = _open(path)
     return _lib
+
+
+_lib_checked = None
+
+
+def load_checked() -> ctypes.CDLL:
+    """Loads the checked build (device-side index and alignment checks,
+    NaN-poisoned padding), building it first if needed; pass it to Solver or
+    Batch as `lib=` (tests)."""
+    global _lib_checked
+    with _lock:
+        if _lib_checked is None:
+            if not _build.up_to_date(checked=True):
+                _build.build(checked=True)
+            _lib_checked = _open(_build.LIB_CHECKED)
+    return _lib_checked
 
 
 class SweError(RuntimeError):
@@ -196,8 +216,8 @@ def _info(i: swe_step_info) -> StepInfo:
 class Solver:
     """One grid on one GPU: owns a swe_ctx."""
 
-    def __init__(self, nx, ny, **kw):
-        self.lib = load()
+    def __init__(self, nx, ny, lib=None, **kw):
+        self.lib = lib if lib is not None else load()
         self.params = make_params(nx, ny, **kw)
         self.nx, self.ny = int(nx), int(ny)
         ctx = ctypes.c_void_p()
@@ -347,8 +367,8 @@ def _torch_check(a, s: Solver):
 class Batch:
     """Many scenarios advanced together (FP32): owns a swe_batch."""
 
-    def __init__(self, sizes, manning_n, **kw):
-        self.lib = load()
+    def __init__(self, sizes, manning_n, lib=None, **kw):
+        self.lib = lib if lib is not None else load()
         kw.setdefault("precision", SWE_FP32)
         self.params = make_params(1, 1, **kw)
         self.sizes = [(int(nx), int(ny)) for nx, ny in sizes]
