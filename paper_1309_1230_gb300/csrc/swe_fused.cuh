@@ -391,7 +391,7 @@ __device__ __forceinline__ bool all_of(const M& m) {
     return r;
 }
 
-template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int NF, bool WET>
+template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int NF, bool WET, bool PRED_ONLY = false>
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
@@ -780,11 +780,11 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
     };
 
     if (SY > 0) {  // the corrector reads P(C-1) from the buffer the predictor overwrites
-        if (!GEN || k >= 4) corrector();
+        if (!PRED_ONLY && (!GEN || k >= 4)) corrector();
         predictor();
     } else {       // the corrector reads P(C+1), which the predictor produces
         predictor();
-        if (!GEN || k >= 4) corrector();
+        if (!PRED_ONLY && (!GEN || k >= 4)) corrector();
     }
     // the ring slot refilled next was read two rows ago: lean rows come in pairs
     // and sync after the second
@@ -834,10 +834,15 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
         issue_pair<T, CPT>(I, q + 2, tme, tmu, tmv, tmz, q + 2 < np);
         if (!wait_pair<T, CPT>(I, q)) { timed_out = true; drain_from = q; issued = min(np, q + 3); break; }
         if (k >= klo && k < khi) {
-#define SWE_PAIR(NF, W)                                                                                           \
-    row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);     \
-    row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
-            if (A.n2 != nullptr) { SWE_PAIR(1, TRY_WET); } else { SWE_PAIR(0, TRY_WET); }
+#define SWE_PAIR(NF, W, PO)                                                                                       \
+    row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W, PO>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet); \
+    row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W, PO>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
+            // the item's first lean pair (k = 2, 3) has no corrector rows yet
+            if (A.n2 != nullptr) {
+                if (k < 4) { SWE_PAIR(1, TRY_WET, true); } else { SWE_PAIR(1, TRY_WET, false); }
+            } else {
+                if (k < 4) { SWE_PAIR(0, TRY_WET, true); } else { SWE_PAIR(0, TRY_WET, false); }
+            }
 #undef SWE_PAIR
         } else {
             row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);
