@@ -383,6 +383,21 @@ __device__ __forceinline__ const unsigned char* slot_clamped(const ItemCtx<T, CP
 // the predicted and the new cells), so that the caller recomputes the item
 // without it where it fails.  Without it, `ok` collects whether every new
 // cell the item outputs is wet (the hint for the next step).
+// The checks of the all-wet assumption keep the running minimum of the
+// depths they cover; NaN propagates (min.NaN), so "every depth > h_dry" is
+// the minimum > h_dry, NaN included, in one instruction per depth.
+__device__ __forceinline__ float nanmin(float a, float b) {
+    float d;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ double nanmin(double a, double b) { return (a != a) ? a : ((b != b) ? b : fmin(a, b)); }
+template <class R, class T>
+__device__ __forceinline__ void chk_min(T& mn, const R& v) {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(R) / sizeof(T)); ++i) mn = nanmin(mn, v[i]);
+}
+
 template <class M>
 __device__ __forceinline__ bool all_of(const M& m) {
     bool r = true;
@@ -395,7 +410,7 @@ template <class T, int CPT, int SX, int SY, bool KAPPA, int PAR, bool GEN, int N
 __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, const ItemCtx<T, CPT>& I, int k,
                                          Carry<T, CPT>& Cy, ItemAcc<T>& ia, const CUtensorMap* tme,
                                          const CUtensorMap* tmu, const CUtensorMap* tmv, const CUtensorMap* tmz,
-                                         bool& timed_out, bool& ok, bool wet) {
+                                         bool& timed_out, T& mn, bool wet) {
     constexpr bool WA = WET && !GEN;  // wet arithmetic: the lean row without selects
     const bool ck = GEN ? wet : WET;  // check the all-wet assumption
     using V = Vec<T, CPT>;
@@ -450,7 +465,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         if (r - 2 < 0) ghost_row(R2, SIDE_S, G); else if (r - 2 >= ny) ghost_row(R2, SIDE_N, G);
     }
     const V h0 = R0.e - R0.z, h1 = R1.e - R1.z, h2 = R2.e - R2.z;
-    if (ck) ok = ok && all_of(h0 > hdv);  // each level-n row of the window enters once as row r
+    if (ck) chk_min(mn, h0);  // each level-n row of the window enters once as row r
 
     // -------- y switch of row r-1, y dissipation flux through the face between
     // rows r-2 and r-1 (north face of the corrector's row, south face of the predictor's)
@@ -491,7 +506,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         const V hxn = xn.e - xn.z;
         const V qxn = hxn * xn.u;
         const V qyn = hyn * yn.v;
-        if (WA) ok = ok && hxn[SX > 0 ? CPT - 1 : 0] > hd;  // the ring's halo cell
+        if (WA) mn = nanmin(mn, hxn[SX > 0 ? CPT - 1 : 0]);  // the ring's halo cell
         V fe, fw, fn, fs;
         if (SX > 0) { fe = qxn; fw = qx; } else { fe = qx; fw = qxn; }
         if (SY > 0) { fn = qyn; fs = qy; } else { fn = qy; fs = qyn; }
@@ -546,7 +561,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         P.e = eo; P.u = uo; P.v = vo; P.z = c.z;
         const V hp = eo - c.z;
         P.qy = hp * vo;
-        if (ck && (!GEN || (p >= 0 && p < ny))) ok = ok && all_of(hp > hdv);  // every lane's predicted cells feed a corrector
+        if (ck && (!GEN || (p >= 0 && p < ny))) chk_min(mn, hp);  // every lane's predicted cells feed a corrector
         if (KAPPA) {
             // x dissipation of row r-1; the outer neighbour on the other side
             // from the ring as well
@@ -559,7 +574,7 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
             const Row<T, CPT>& L = SX > 0 ? xo : xn;  // left neighbours
             const Row<T, CPT>& Rr = SX > 0 ? xn : xo; // right neighbours
             V hl = L.e - L.z, hr = Rr.e - Rr.z;
-            if (WA) ok = ok && (SX > 0 ? hl[0] : hr[CPT - 1]) > hd;  // the ring's other halo cell
+            if (WA) mn = nanmin(mn, SX > 0 ? hl[0] : hr[CPT - 1]);  // the ring's other halo cell
             if (edge) {  // ghost depth at columns -1 and nx is the adjacent interior depth
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) {
@@ -708,10 +723,10 @@ __device__ __forceinline__ void row_step(const ItemIO<T>& A, const StepK<T>& S, 
         // the new cells the item outputs are wet (the fix below keeps a cell
         // whose depth is above h_dry as it is)
         const V hn = oe - cs.z;
-        bool wn = true;
+        T wn = T(INFINITY);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) wn = wn && ((edge && I.x0c + j >= nx) || hn[j] > hd);
-        ok = ok && (!st || wn);
+        for (int j = 0; j < CPT; ++j) wn = nanmin(wn, (edge && I.x0c + j >= nx) ? T(INFINITY) : hn[j]);
+        mn = st ? nanmin(mn, wn) : mn;
         V ad;
         if (WA) ad = V(T(0));
         else ad = wetdry_fix(oe, ou, ov, cs.z, hd);
@@ -814,7 +829,9 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
     ia.bad = false;
 #pragma unroll
     for (int q = 0; q < 4; ++q) ia.side[q * 32] = T(0);
-    bool ok = true, held = true;
+    T mn = T(INFINITY);  // the minimum of the depths checked (ok: mn > h_dry)
+    bool held = true;
+    const T hdc = A.G.h_dry;
     int drain_from = 0, issued = 0;  // after a failed wait or check: the pairs to drain, [drain_from, issued)
     int k = 0;
     const int ny = A.G.ny;
@@ -835,8 +852,8 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
         if (!wait_pair<T, CPT>(I, q)) { timed_out = true; drain_from = q; issued = min(np, q + 3); break; }
         if (k >= klo && k < khi) {
 #define SWE_PAIR(NF, W, PO)                                                                                       \
-    row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W, PO>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet); \
-    row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W, PO>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet)
+    row_step<T, CPT, SX, SY, KAPPA, 0, false, NF, W, PO>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, mn, wet); \
+    row_step<T, CPT, SX, SY, KAPPA, 1, false, NF, W, PO>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out, mn, wet)
             // the item's first lean pair (k = 2, 3) has no corrector rows yet
             if (A.n2 != nullptr) {
                 if (k < 4) { SWE_PAIR(1, TRY_WET, true); } else { SWE_PAIR(1, TRY_WET, false); }
@@ -845,16 +862,16 @@ __device__ __forceinline__ int run_rows(const ItemIO<T>& A, const StepK<T>& S, I
             }
 #undef SWE_PAIR
         } else {
-            row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, ok, wet);
+            row_step<T, CPT, SX, SY, KAPPA, 0, true, 0, false>(A, S, I, k, Cy, ia, tme, tmu, tmv, tmz, timed_out, mn, wet);
             if (k + 1 < nr)  // the last row of an odd count runs alone
                 row_step<T, CPT, SX, SY, KAPPA, 1, true, 0, false>(A, S, I, k + 1, Cy, ia, tme, tmu, tmv, tmz, timed_out,
-                                                                   ok, wet);
+                                                                   mn, wet);
         }
-        if (TRY_WET && wet && !__all_sync(FULL, ok)) {
+        if (TRY_WET && wet && !__all_sync(FULL, mn > hdc)) {
             held = false; drain_from = q + 1; issued = min(np, q + 3); break;
         }
     }
-    const bool all_ok = held && __all_sync(FULL, ok);
+    const bool all_ok = held && __all_sync(FULL, mn > hdc);
     if (TRY_WET && wet && held && !timed_out && !all_ok) { held = false; drain_from = np; issued = np; }
     if (timed_out || !held) {
         // drain this pass's loads still in flight (bounded) before the ring is reused or left
