@@ -98,3 +98,17 @@ def test_kernel_hash_ignores_comments_only():
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(c)
     assert "not a comment" in bench._code_only(a)
+
+
+def test_checked_build_compiles_and_exports_the_abi():
+    """The checked build (-DSWE_CHECKED: device-side index and alignment
+    checks, NaN-poisoned planes) cross-compiles for sm_103a and exports the
+    same entry points; the GPU test of what it checks is test_gpu_checked.py."""
+    from paper_1309_1230_gb300 import _build, swe
+    path = _build.build(checked=True)
+    assert path == _build.LIB_CHECKED and os.path.exists(path)
+    chk = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, f"declared but not exported by the checked build: {missing}"
+    chk.swe_status_string.restype = ctypes.c_char_p
+    assert chk.swe_status_string(swe.SWE_ERR_CHECK).decode() == "device-side check failed"
