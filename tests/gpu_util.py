@@ -41,7 +41,7 @@ def rel_err(a, b, floor=1e-300):
 # its maximum; velocities: the largest velocity component of the flow, at
 # least 1e-3 m/s, so that a component that is nearly zero everywhere, such
 # as v in a narrow channel, is measured against the flow and not against its
-# own rounding).  Depth: the benchmark spec's 1e-4 in the max norm and 1e-5 in
+# own rounding).  Depth: 1e-4 of the maximum depth in the max norm and 1e-5 in
 # L2.  Velocities: the pressure term differences elevations of ~1-10 m stored
 # with ~5e-7 m of rounding, so every step adds ~g dt/dx * 1e-6 m/s of noise
 # (~5e-7 m/s); over a few hundred steps that is ~1e-5 m/s against velocities
